@@ -1,0 +1,137 @@
+/*
+ * mb.h -- C ABI of the GB300 escape-time (Mandelbrot) renderer.
+ *
+ * The library computes, for every pixel (i, j) of an m x n image, the Boolean
+ * escape-time count of Sec. I of "Efficient Generation of Mandelbrot Set using
+ * Message Passing Interface" (Eq. 1: f(z) = z^2 + c iterated from z = 0;
+ * Eq. 2: I_{i,j} = Iteration_{i,j}): the number of z-updates made before the
+ * first iterate with |z|^2 > R^2, or iterMax if there is none.  Every count is
+ * bit-identical to a plain IEEE binary64 evaluation in this order:
+ *     zr2 = zr*zr; zi2 = zi*zi; if (zr2 + zi2 > R2) stop;
+ *     zi = (2*zr)*zi + ci; zr = (zr2 - zi2) + cr;
+ * with the pixel map (the Cx / Cy arrays of Sec. III-A)
+ *     c_re(j) = xmin + (j*(xmax - xmin))/n,  c_im(i) = ymax - (i*(ymax - ymin))/m,
+ * each operation rounded to nearest-even on its own (no fused multiply-add).
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: MB_OK (0) or one of the MB_E* codes below; mb_strerror()
+ *    names them.  Arguments are validated before anything is launched; an
+ *    invalid call changes no memory.
+ *  - Pointers documented as "device" must point to memory of the current CUDA
+ *    device; "host" pointers to ordinary (or pinned) host memory.  The library
+ *    never frees memory it did not allocate.
+ *  - Launches are asynchronous on the stream given in mb_opts (NULL = the
+ *    legacy default stream); results are valid once that stream is synchronised.
+ *  - Temporary device memory the library needs (the Cx/Cy arrays, work
+ *    counters) comes from opts->workspace when given, else from
+ *    cudaMallocAsync/cudaFreeAsync on the same stream.
+ *  - Counts are uint32, row-major, out[i*n + j]; row 0 is the top (c_im = ymax).
+ */
+#ifndef MB_H
+#define MB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MB_OK 0
+#define MB_EINVAL 1      /* bad argument: zero size, non-finite or empty window, R2 <= 0, NULL output */
+#define MB_ENOMEM 2      /* device or host allocation failed, or a memory budget would be exceeded */
+#define MB_ECUDA 3       /* a CUDA runtime call failed */
+#define MB_ETIMEDOUT 4   /* a bounded wait ran out */
+#define MB_EBUSY 5       /* a server queue is full */
+#define MB_ENOTFOUND 6   /* unknown request id */
+#define MB_EDEVICE 7     /* a kernel reported an internal error in its status word */
+
+/* Complex window: c_re spans [xmin, xmax), c_im spans (ymin, ymax]. */
+typedef struct {
+  double xmin, xmax, ymin, ymax;
+} mb_window;
+
+/* Row / tile schedulers: the paper's three partition schemes (Sec. III) run as
+ * on-device schedulers.  A "worker" is one CTA; its warps share the worker's
+ * pixels and refill a lane as soon as that lane's pixel finishes. */
+typedef enum {
+  MB_SCHED_NAIVE = 0,        /* Sec. III-A: CTA b of G owns rows [b*(m/G), (b+1)*(m/G)), the last CTA also the m mod G rest */
+  MB_SCHED_ALTERNATING = 1,  /* Sec. III-C: CTA b owns rows b, b+G, b+2G, ... */
+  MB_SCHED_FCFS_ROWS = 2,    /* Sec. III-B: persistent CTAs take the next row from a global atomic counter */
+  MB_SCHED_FCFS_TILES = 3,   /* as FCFS_ROWS, with tile x tile blocks in raster order as work items */
+  MB_SCHED_FCFS_ITEMS = 4    /* as FCFS_TILES, over a caller-given device list of mb_item (e.g. longest-first) */
+} mb_sched;
+
+/* One work item of MB_SCHED_FCFS_ITEMS: rows [row0, row0+rows) of tile `tile`
+ * (tiles numbered row-major, tile x tile pixels, cut at the image edge). */
+typedef struct {
+  uint32_t tile;
+  uint16_t row0;
+  uint16_t rows;
+} mb_item;
+
+/* Per-CTA trace record written when opts->trace is given (globaltimer ns). */
+typedef struct {
+  uint64_t start_ns;
+  uint64_t end_ns;
+  uint32_t smid;
+  uint32_t items;    /* work items (rows / tiles / list entries) this CTA took */
+} mb_cta_trace;
+
+typedef struct {
+  int sched;                 /* mb_sched; default MB_SCHED_FCFS_TILES */
+  uint32_t tile;             /* tile side, a power of two in [8, 256]; 0 = 64 */
+  uint32_t grid;             /* CTAs; 0 = SM count x resident CTAs per SM */
+  uint32_t block;            /* threads per CTA, multiple of 32 in [32, 512]; 0 = 256 */
+  uint32_t unroll;           /* escape steps between lane refills: 4, 8 or 16; 0 = 8 */
+  void* stream;              /* cudaStream_t; NULL = legacy default stream */
+  const mb_item* items;      /* device; required for MB_SCHED_FCFS_ITEMS */
+  uint32_t n_items;
+  uint64_t* tile_totals;     /* device, optional: += sum of counts per tile (row-major tiles); caller zeroes it */
+  mb_cta_trace* trace;       /* device, optional: one record per CTA, for CTAs below trace_len */
+  uint32_t trace_len;        /* records available at `trace` */
+  uint32_t* status;          /* device, optional: kernels OR error bits into it (0 = fine) */
+  void* workspace;           /* device, optional: temporary memory, >= mb_render_workspace_size() bytes, 256-byte aligned */
+  size_t workspace_bytes;
+} mb_opts;
+
+/* Library version string. */
+const char* mb_version(void);
+
+/* Human-readable name of a return code. */
+const char* mb_strerror(int code);
+
+/* Render one image (Eq. 2 for all i < m, j < n).
+ *   w        host; the complex window (finite, xmin < xmax, ymin < ymax)
+ *   m, n     rows and columns, each in [1, 2^20]; fewer than 2^32 - 1 tiles
+ *   iter_max iteration budget per pixel (0 allowed: every count is 0)
+ *   escape_r2  squared escape radius R^2, finite and > 0
+ *   out      device, m*n uint32, written in full
+ *   opt      host, may be NULL (all defaults)
+ * Errors: MB_EINVAL for bad arguments; MB_ENOMEM / MB_ECUDA from the launch. */
+int mb_render(const mb_window* w, uint32_t m, uint32_t n, uint32_t iter_max, double escape_r2,
+              uint32_t* out, const mb_opts* opt);
+
+/* Bytes of temporary device memory mb_render needs for this size and options
+ * (Cx/Cy arrays and work counters), so that a caller can pass opts->workspace. */
+size_t mb_render_workspace_size(uint32_t m, uint32_t n, const mb_opts* opt);
+
+/* Sum of `count` uint32 values (device) into *total (device uint64, overwritten),
+ * i.e. the number of z-updates of a rendered image. */
+int mb_sum_counts(const uint32_t* counts, uint64_t count, uint64_t* total, void* stream);
+
+/* FP64 issue-rate microbenchmark: runs independent chains of one binary64
+ * operation (op: 0 = add, 1 = mul, 2 = fma) on every SM and returns the
+ * measured rate in operations per second (a fused multiply-add counts as one
+ * operation) and the elapsed kernel time.  Synchronous.  This rate is the
+ * denominator of "% of FP64 peak". */
+int mb_fp64_peak(int op, double* ops_per_s, double* seconds);
+
+/* Number of SMs and resident CTAs per SM the render kernel gets at `block` threads. */
+int mb_device_info(uint32_t block, uint32_t* sms, uint32_t* ctas_per_sm);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MB_H */

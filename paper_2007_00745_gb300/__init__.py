@@ -1,0 +1,122 @@
+"""GB300-native escape-time (Mandelbrot) renderer: Python binding of libmb.so.
+
+The functions below carry the names of the C entry points in include/mb.h and
+only marshal arguments: torch tensors provide device memory and streams, the
+CUDA library does every step of the computation.  Importing this package does
+not load the library; the first call does, and fails loudly if it is missing.
+"""
+import ctypes
+
+__all__ = [
+    "mb_version", "mb_strerror", "mb_render", "mb_render_workspace_size", "mb_sum_counts",
+    "mb_fp64_peak", "mb_device_info", "Window", "MBError",
+]
+
+MB_SCHED_NAIVE, MB_SCHED_ALTERNATING, MB_SCHED_FCFS_ROWS, MB_SCHED_FCFS_TILES, MB_SCHED_FCFS_ITEMS = range(5)
+SCHEDS = {"naive": MB_SCHED_NAIVE, "alternating": MB_SCHED_ALTERNATING, "fcfs_rows": MB_SCHED_FCFS_ROWS,
+          "fcfs_tiles": MB_SCHED_FCFS_TILES, "fcfs_items": MB_SCHED_FCFS_ITEMS}
+
+
+def _L():
+    from . import _lib
+    return _lib
+
+
+class MBError(RuntimeError):
+    pass
+
+
+def Window(xmin, xmax, ymin, ymax):
+    return (float(xmin), float(xmax), float(ymin), float(ymax))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _opts(sched="fcfs_tiles", tile=0, grid=0, block=0, unroll=0, stream=None, items=None, n_items=0,
+          tile_totals=None, trace=None, trace_len=0, status=None, workspace=None, workspace_bytes=0):
+    L = _L()
+    o = L.mb_opts()
+    o.sched = SCHEDS[sched] if isinstance(sched, str) else int(sched)
+    o.tile, o.grid, o.block, o.unroll = int(tile), int(grid), int(block), int(unroll)
+    o.stream = _stream(stream)
+    o.items = _ptr(items)
+    o.n_items = int(n_items if n_items else (items.numel() // 2 if items is not None and hasattr(items, "numel") else 0))
+    o.tile_totals = _ptr(tile_totals)
+    o.trace = _ptr(trace)
+    o.trace_len = int(trace_len if trace_len else (trace.numel() * trace.element_size() // 24
+                                                   if trace is not None and hasattr(trace, "numel") else 0))
+    o.status = _ptr(status)
+    o.workspace = _ptr(workspace)
+    o.workspace_bytes = int(workspace_bytes if workspace_bytes else
+                            (workspace.numel() * workspace.element_size() if workspace is not None
+                             and hasattr(workspace, "numel") else 0))
+    return o
+
+
+def _check(rc, where):
+    if rc != 0:
+        L = _L()
+        err = MBError("%s: %s (%d)" % (where, L.lib().mb_strerror(rc).decode(), rc))
+        err.code = rc
+        raise err
+
+
+def mb_version():
+    return _L().lib().mb_version().decode()
+
+
+def mb_strerror(code):
+    return _L().lib().mb_strerror(int(code)).decode()
+
+
+def mb_render(window, m, n, iter_max, escape_r2, out, **opts):
+    """Render an m x n image of escape counts into the device tensor `out`
+    (int32/uint32, m*n elements).  Keyword options mirror mb_opts."""
+    L = _L()
+    w = L.mb_window(*map(float, window))
+    o = _opts(**opts)
+    rc = L.lib().mb_render(ctypes.byref(w), int(m), int(n), int(iter_max), float(escape_r2), _ptr(out),
+                           ctypes.byref(o))
+    _check(rc, "mb_render")
+
+
+def mb_render_workspace_size(m, n, **opts):
+    L = _L()
+    o = _opts(**opts)
+    return int(L.lib().mb_render_workspace_size(int(m), int(n), ctypes.byref(o)))
+
+
+def mb_sum_counts(counts, total, stream=None):
+    """Sum of the uint32 counts in device tensor `counts` into device int64 tensor `total`."""
+    _check(_L().lib().mb_sum_counts(_ptr(counts), int(counts.numel()), _ptr(total), _stream(stream)),
+           "mb_sum_counts")
+
+
+def mb_fp64_peak(op=0):
+    """(binary64 operations per second, seconds) of the FP64 issue-rate microbenchmark."""
+    L = _L()
+    r, s = ctypes.c_double(), ctypes.c_double()
+    _check(L.lib().mb_fp64_peak(int(op), ctypes.byref(r), ctypes.byref(s)), "mb_fp64_peak")
+    return r.value, s.value
+
+
+def mb_device_info(block=0):
+    L = _L()
+    a, b = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(L.lib().mb_device_info(int(block), ctypes.byref(a), ctypes.byref(b)), "mb_device_info")
+    return a.value, b.value

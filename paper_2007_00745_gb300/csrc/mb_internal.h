@@ -1,0 +1,34 @@
+// mb_internal.h -- declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mb.h"
+
+namespace mb {
+
+constexpr uint32_t MAX_SIDE = 1u << 20;
+constexpr uint32_t DEFAULT_TILE = 64;
+constexpr uint32_t DEFAULT_BLOCK = 256;
+constexpr uint32_t DEFAULT_UNROLL = 8;
+
+enum ItemKind : int { KIND_ROWS = 0, KIND_RASTER = 1, KIND_LIST = 2, KIND_BATCH = 3 };
+enum SchedKind : int { S_NAIVE = 0, S_ALT = 1, S_FCFS = 2 };
+
+struct RenderParams;
+struct EscThr;
+using RenderFn = void (*)(RenderParams);
+
+bool filter_ok(double r2);
+EscThr make_thr(double r2);
+int check_view(const mb_window* w, uint32_t m, uint32_t n, double r2, const void* out);
+int check_opts(const mb_opts* o, uint32_t* log2_tile);
+RenderFn render_fn(int kind, int sched, bool filt, int unroll);
+int launch_render(const RenderFn fn, const RenderParams& P, uint32_t grid, uint32_t block, cudaStream_t st);
+uint32_t default_grid(RenderFn fn, uint32_t block);
+int sm_count();
+int resident_ctas(const void* fn, int block);
+
+inline int opt_unroll(const mb_opts* o) { return o && o->unroll ? (int)o->unroll : (int)DEFAULT_UNROLL; }
+
+}  // namespace mb

@@ -1,0 +1,312 @@
+// render_kernels.cuh -- pixel map and the scheduled escape-time render kernel.
+//
+// One kernel family serves every scheduler of the paper's Sec. III and the
+// batched / served modes.  A worker is one CTA.  The CTA keeps one 64-bit
+// word in shared memory, (current item id : next pixel offset); a warp with
+// idle lanes claims that many pixels with one shared atomicAdd.  The warp whose
+// claim reaches the end of the item fetches the CTA's next item -- statically
+// for the naive (Sec. III-A) and alternating (Sec. III-C) partitions, from a
+// global atomic counter for first-come-first-served (Sec. III-B) -- and
+// publishes it with one atomicExch; warps that claimed past the end wait
+// (bounded) for that word to change and claim again.  A lane whose pixel
+// finishes stores its count and takes a fresh pixel at the next refill, so
+// lanes stay busy although trip counts differ wildly between pixels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "escape_core.cuh"
+#include "mb.h"
+#include "mb_internal.h"
+
+namespace mb {
+
+// Per-view constants, in device memory.
+struct ViewDesc {
+  const double* cx;     // n entries: c_re of each column
+  const double* cy;     // m entries: c_im of each row
+  uint32_t* out;        // m*n counts
+  uint64_t* totals;     // per-tile sums of counts (may be null)
+  double xmin, xmax, ymin, ymax;
+  double r2;
+  EscThr thr;
+  uint32_t m, n, iter_max, tiles_x, tiles_y;
+  uint32_t pad_;
+};
+
+// Work item of the batched list: rows [row0, row0+rows) of tile `tile` of view `view`.
+struct BatchItem {
+  uint32_t view;
+  uint32_t tile;
+  uint16_t row0, rows;
+};
+
+
+// status bits
+constexpr uint32_t ST_SPIN_TIMEOUT = 1u;
+constexpr uint32_t ST_BAD_ITEM = 2u;
+
+constexpr uint32_t END_ITEM = 0xFFFFFFFFu;
+constexpr int SPIN_LIMIT = 1 << 22;  // ~0.3 s at 64 ns per try: far above any real wait
+
+struct RenderParams {
+  const ViewDesc* views;
+  const mb_item* items;        // KIND_LIST
+  const BatchItem* bitems;     // KIND_BATCH
+  uint32_t n_items;            // rows (KIND_ROWS), tiles (KIND_RASTER) or list length
+  uint32_t log2_tile;
+  uint32_t* counter;           // FCFS work counter (zeroed before launch)
+  uint32_t* status;            // error bits (may be null)
+  mb_cta_trace* trace;         // per-CTA record (may be null)
+  uint32_t trace_len;          // records available at `trace`
+};
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t smid() {
+  uint32_t s;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(s));
+  return s;
+}
+
+__device__ __forceinline__ void set_status(const RenderParams& P, uint32_t bits) {
+  if (P.status) atomicOr(P.status, bits);
+}
+
+// Pixels in item `it` (before edge clipping).
+template <int KIND>
+__device__ __forceinline__ uint32_t item_pixels(const RenderParams& P, uint32_t it) {
+  if (KIND == KIND_ROWS) return P.views[0].n;
+  if (KIND == KIND_RASTER) return 1u << (2 * P.log2_tile);
+  if (KIND == KIND_LIST) return (uint32_t)P.items[it].rows << P.log2_tile;
+  return (uint32_t)P.bitems[it].rows << P.log2_tile;
+}
+
+// First item of CTA b, and the item after `it`.
+template <int SCHED>
+__device__ __forceinline__ uint32_t first_item(const RenderParams& P) {
+  uint32_t G = gridDim.x, b = blockIdx.x, N = P.n_items;
+  if (SCHED == S_NAIVE) {  // S_b = (N/G) b; the last CTA also takes N mod G (Sec. III-A)
+    uint32_t per = N / G;
+    uint32_t cnt = per + (b == G - 1 ? N % G : 0);
+    return cnt ? per * b : END_ITEM;
+  }
+  if (SCHED == S_ALT) return b < N ? b : END_ITEM;  // rows b, b+G, ... (Sec. III-C)
+  uint32_t k = atomicAdd(P.counter, 1u);             // Sec. III-B
+  return k < N ? k : END_ITEM;
+}
+
+template <int SCHED>
+__device__ __forceinline__ uint32_t next_item(const RenderParams& P, uint32_t it) {
+  uint32_t G = gridDim.x, b = blockIdx.x, N = P.n_items;
+  if (SCHED == S_NAIVE) {
+    uint32_t per = N / G;
+    uint32_t last = per * (b + 1) + (b == G - 1 ? N % G : 0);
+    return it + 1 < last ? it + 1 : END_ITEM;
+  }
+  if (SCHED == S_ALT) return it + G < N ? it + G : END_ITEM;
+  uint32_t k = atomicAdd(P.counter, 1u);
+  return k < N ? k : END_ITEM;
+}
+
+// Claim up to `need` pixels for the calling warp (lane 0 only).  Returns the
+// number granted (0 = no work left) and the item / first offset.
+template <int KIND, int SCHED>
+__device__ uint32_t claim(const RenderParams& P, unsigned long long* word, uint32_t* taken, uint32_t need,
+                          uint32_t& item, uint32_t& off) {
+  int spins = 0;
+  for (;;) {
+    unsigned long long w = atomicAdd(word, (unsigned long long)need);
+    uint32_t it = (uint32_t)(w >> 32), o = (uint32_t)w;
+    if (it == END_ITEM) return 0;
+    uint32_t Pn = item_pixels<KIND>(P, it);
+    if (o < Pn) {
+      item = it;
+      off = o;
+      if (o + need >= Pn) {  // this claim reaches the item's end: advance the CTA
+        uint32_t nx = next_item<SCHED>(P, it);
+        if (nx != END_ITEM) atomicAdd(taken, 1u);
+        atomicExch(word, (unsigned long long)nx << 32);
+        return Pn - o;
+      }
+      return need;
+    }
+    // Claimed past the end: another warp is fetching the next item.
+    while ((uint32_t)(*(volatile unsigned long long*)word >> 32) == it) {
+      if (++spins > SPIN_LIMIT) {
+        set_status(P, ST_SPIN_TIMEOUT);
+        return 0;
+      }
+      __nanosleep(64);
+    }
+  }
+}
+
+// Map pixel `pix` of item `it` to (view, row, col); false if it lies outside the image.
+template <int KIND>
+__device__ __forceinline__ bool decode(const RenderParams& P, uint32_t it, uint32_t pix, uint32_t& v,
+                                       uint32_t& row, uint32_t& col, uint32_t& tile) {
+  if (KIND == KIND_ROWS) {
+    v = 0;
+    row = it;
+    col = pix;
+    tile = 0;
+    return true;
+  }
+  uint32_t t, r0;
+  if (KIND == KIND_RASTER) {
+    v = 0;
+    t = it;
+    r0 = 0;
+  } else if (KIND == KIND_LIST) {
+    v = 0;
+    mb_item e = P.items[it];
+    t = e.tile;
+    r0 = e.row0;
+  } else {
+    BatchItem e = P.bitems[it];
+    v = e.view;
+    t = e.tile;
+    r0 = e.row0;
+  }
+  if ((r0 + (pix >> P.log2_tile)) >> P.log2_tile) {  // item reaches past its tile
+    if (P.status) atomicOr(P.status, ST_BAD_ITEM);
+    return false;
+  }
+  const ViewDesc& V = P.views[v];
+  uint32_t ty = t / V.tiles_x, tx = t - ty * V.tiles_x;
+  row = (ty << P.log2_tile) + r0 + (pix >> P.log2_tile);
+  col = (tx << P.log2_tile) + (pix & ((1u << P.log2_tile) - 1u));
+  tile = t;
+  return ty < V.tiles_y && row < V.m && col < V.n;
+}
+
+template <int KIND, int SCHED, bool FILT, int UNROLL>
+__global__ void __launch_bounds__(512) render_kernel(RenderParams P) {
+  __shared__ unsigned long long s_word;
+  __shared__ uint32_t s_taken;
+  const int lane = threadIdx.x & 31;
+  uint64_t t_start = 0;
+  if (threadIdx.x == 0) {
+    t_start = globaltimer_ns();
+    uint32_t it = first_item<SCHED>(P);
+    s_word = (unsigned long long)it << 32;
+    s_taken = it != END_ITEM ? 1u : 0u;
+  }
+  __syncthreads();
+
+  Lane L;
+  L.zr = L.zi = L.cr = L.ci = 0.0;
+  L.cnt = 0;
+  L.lim = 0;
+  L.live = false;
+  bool has = false;
+  bool drained = false;
+  uint32_t* optr = nullptr;
+  uint64_t* tptr = nullptr;
+  double r2 = 4.0;
+  EscThr thr{3.99f, 4.01f};
+
+  for (;;) {
+    // Retire finished pixels.
+    if (has && !L.live) {
+      *optr = L.cnt;
+      if (tptr) atomicAdd((unsigned long long*)tptr, (unsigned long long)L.cnt);
+      has = false;
+    }
+    // Refill idle lanes.
+    unsigned idle = __ballot_sync(FULL_MASK, !has);
+    while (idle && !drained) {
+      uint32_t need = __popc(idle), item = 0, off = 0, got = 0;
+      if (lane == 0) got = claim<KIND, SCHED>(P, &s_word, &s_taken, need, item, off);
+      got = __shfl_sync(FULL_MASK, got, 0);
+      if (got == 0) {
+        drained = true;
+        break;
+      }
+      item = __shfl_sync(FULL_MASK, item, 0);
+      off = __shfl_sync(FULL_MASK, off, 0);
+      uint32_t rank = __popc(idle & ((1u << lane) - 1u));
+      if (!has && rank < got) {
+        uint32_t v, row, col, tile;
+        if (decode<KIND>(P, item, off + rank, v, row, col, tile)) {
+          const ViewDesc& V = P.views[v];
+          L.cr = V.cx[col];
+          L.ci = V.cy[row];
+          L.zr = 0.0;
+          L.zi = 0.0;
+          L.cnt = 0;
+          L.lim = V.iter_max;
+          L.live = true;
+          r2 = V.r2;
+          thr = V.thr;
+          optr = V.out + (size_t)row * V.n + col;
+          tptr = V.totals ? V.totals + tile : nullptr;
+          has = true;
+        }
+      }
+      idle = __ballot_sync(FULL_MASK, !has);
+    }
+    if (__ballot_sync(FULL_MASK, has) == 0) break;
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) step<FILT>(L, r2, thr);
+  }
+
+  __syncthreads();
+  if (threadIdx.x == 0 && P.trace && blockIdx.x < P.trace_len) {
+    mb_cta_trace rec;
+    rec.start_ns = t_start;
+    rec.end_ns = globaltimer_ns();
+    rec.smid = smid();
+    rec.items = s_taken;
+    P.trace[blockIdx.x] = rec;
+  }
+}
+
+// Cx / Cy arrays of one or more views (Sec. III-A: every task precomputes them),
+// one view per blockIdx.y.  Also zeroes the FCFS counter.
+static __global__ void pixel_map_kernel(const ViewDesc* views, uint32_t* counter) {
+  const ViewDesc& V = views[blockIdx.y];
+  if (counter && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *counter = 0;
+  double sx = __dsub_rn(V.xmax, V.xmin);
+  double sy = __dsub_rn(V.ymax, V.ymin);
+  double dn = (double)V.n, dm = (double)V.m;
+  double* cx = const_cast<double*>(V.cx);
+  double* cy = const_cast<double*>(V.cy);
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < V.n + V.m; k += gridDim.x * blockDim.x) {
+    if (k < V.n) {
+      cx[k] = __dadd_rn(V.xmin, __ddiv_rn(__dmul_rn((double)k, sx), dn));
+    } else {
+      uint32_t i = k - V.n;
+      cy[i] = __dsub_rn(V.ymax, __ddiv_rn(__dmul_rn((double)i, sy), dm));
+    }
+  }
+}
+
+// Single-view form: takes the descriptor by value and also stores it for the
+// render kernel that follows on the same stream.
+static __global__ void pixel_map_single_kernel(ViewDesc V, ViewDesc* dst, uint32_t* counter) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *dst = V;
+    if (counter) *counter = 0;
+  }
+  double sx = __dsub_rn(V.xmax, V.xmin);
+  double sy = __dsub_rn(V.ymax, V.ymin);
+  double dn = (double)V.n, dm = (double)V.m;
+  double* cx = const_cast<double*>(V.cx);
+  double* cy = const_cast<double*>(V.cy);
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < V.n + V.m; k += gridDim.x * blockDim.x) {
+    if (k < V.n) {
+      cx[k] = __dadd_rn(V.xmin, __ddiv_rn(__dmul_rn((double)k, sx), dn));
+    } else {
+      uint32_t i = k - V.n;
+      cy[i] = __dsub_rn(V.ymax, __ddiv_rn(__dmul_rn((double)i, sy), dm));
+    }
+  }
+}
+
+}  // namespace mb
