@@ -35,8 +35,39 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--sched", default="fcfs_tiles")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-peak", action="store_true", help="skip the FP64 microbenchmark (profiling runs)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-compare", action="store_true", help="skip the per-scheduler makespan comparison")
+    p.add_argument("--size", type=int, default=0, help="override m = n (profiling runs)")
+    p.add_argument("--iter-max", type=int, default=0, help="override iterMax (profiling runs)")
     p.add_argument("--cpu-rows-stride", type=int, default=4)
     return p.parse_args()
+
+
+def bench_view(args):
+    from paper_2007_00745_gb300 import workloads as wl
+    v = wl.FULL_VIEW_2
+    if args.size or args.iter_max:
+        v = wl.scaled(v, args.size or v.m, args.size or v.n, args.iter_max or v.iter_max)
+    return v
+
+
+def trace_stats(tr, sms):
+    """Makespan and idle tail from per-CTA (start, end, smid) records: idle tail =
+    sum over SMs of (makespan - that SM's last end) / (#SMs * makespan)."""
+    import numpy as np
+    start = tr[:, 0].astype(np.int64)
+    end = tr[:, 1].astype(np.int64)
+    smid = (tr[:, 2] & 0xFFFFFFFF).astype(np.int64)
+    t0, t1 = int(start.min()), int(end.max())
+    span = max(t1 - t0, 1)
+    last = np.full(sms, t0, np.int64)
+    for s_, e_ in zip(smid, end):
+        if 0 <= s_ < sms:
+            last[s_] = max(last[s_], e_)
+    idle = float((t1 - last).sum()) / (sms * span)
+    return {"makespan_ms": span / 1e6, "idle_tail": idle,
+            "cta_end_spread_ms": float(end.max() - end.min()) / 1e6}
 
 
 def dist_env():
@@ -123,9 +154,9 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2007_00745_gb300 import workloads as wl
-    v = wl.FULL_VIEW_2
+    v = bench_view(args)
     times, iters = [], 0
-    stride = max(args.cpu_rows_stride * 8, 1)
+    stride = max(args.cpu_rows_stride, 1)
     for k in range(args.warmup + args.steps):
         it, dt, nrows, cores = cpu_sample_parallel(v, stride)
         if k >= args.warmup:
@@ -164,7 +195,7 @@ def run_ours(args):
         import paper_2007_00745_gb300 as mb
     from paper_2007_00745_gb300 import workloads as wl
 
-    v = wl.FULL_VIEW_2
+    v = bench_view(args)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     out = torch.empty(v.m * v.n, dtype=torch.int32, device=dev)
@@ -175,9 +206,12 @@ def run_ours(args):
         mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, out, sched=args.sched, stream=stream)
 
     # FP64 pipe peak (the roofline denominator), measured now on this GPU.
-    peak_add, _ = mb.mb_fp64_peak(0)
-    peak_mul, _ = mb.mb_fp64_peak(1)
-    peak = max(peak_add, peak_mul)
+    if args.no_peak:
+        peak = float("nan")
+    else:
+        peak_add, _ = mb.mb_fp64_peak(0)
+        peak_mul, _ = mb.mb_fp64_peak(1)
+        peak = max(peak_add, peak_mul)
 
     step()
     mb.mb_sum_counts(out, total, stream=stream)
@@ -210,7 +244,7 @@ def run_ours(args):
 
     # end to end through the public call with host buffers: render + D2H of the counts
     e2e_ms = []
-    for k in range(max(2, min(args.steps, 3))):
+    for k in range(0 if args.no_e2e else max(2, min(args.steps, 3))):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record(stream)
@@ -228,7 +262,25 @@ def run_ours(args):
     value = ws * iters / (ms_step * 1e-3) / 1e9
     k_ms = sum(kernel_ms) / len(kernel_ms)
     achieved = iters * ALG_OPS_PER_ITER / (k_ms * 1e-3) / 1e12
-    e2e_val = ws * iters / (sum(e2e_ms) / len(e2e_ms) * 1e-3) / 1e9
+    e2e_val = ws * iters / (sum(e2e_ms) / len(e2e_ms) * 1e-3) / 1e9 if e2e_ms else None
+
+    # Makespan of each scheduler on the same view (outside the timed region).
+    compare = {}
+    if not args.no_compare:
+        sms, _ = mb.mb_device_info(256)
+        for sched in ("naive", "alternating", "fcfs_rows", "fcfs_tiles"):
+            g = sms * mb.mb_device_info(256)[1]
+            tr = torch.zeros(g * 3, dtype=torch.int64, device=dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, out, sched=sched, stream=stream, grid=g,
+                         trace=tr)
+            b.record(stream)
+            torch.cuda.synchronize()
+            st = trace_stats(tr.cpu().numpy().reshape(-1, 3), sms)
+            st["ms"] = a.elapsed_time(b)
+            st["giter_s"] = iters / (st["ms"] * 1e-3) / 1e9
+            compare[sched] = st
 
     if rank != 0:
         if ws > 1:
@@ -239,10 +291,12 @@ def run_ours(args):
         "metric": "Giter/s", "value": value, "unit": "Giter/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "8192x8192 re[-2,1] im[-1.5,1.5] iterMax 10000 R2 4, sched %s" % args.sched,
+        "config": {"workload": "%dx%d re[-2,1] im[-1.5,1.5] iterMax %d R2 4, sched %s"
+                               % (v.m, v.n, v.iter_max, args.sched),
                    "iterations_per_step": iters, "l2": "output 268 MB > 129 MB L2 per step",
                    "parallelism": "replicas" if ws > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak / 1e12, "unit": "TFLOP/s",
+                     "peak_source": "mb_fp64_peak: binary64 add/mul issue rate measured in this run",
                      "frac": achieved / (peak / 1e12), "traffic": None,
                      "note": "binary64 ops: 8 per escape step; peak = measured FP64 issue rate (mb_fp64_peak)"},
         "pct_fp64_peak": 100.0 * achieved / (peak / 1e12),
@@ -251,9 +305,10 @@ def run_ours(args):
         "e2e": {"value": e2e_val, "unit": "Giter/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": v.m * v.n * 4},
         "gpu_launches": 2 * args.steps,
+        "schedulers": compare,
     }
     if not args.no_cpu_baseline:
-        stride = max(args.cpu_rows_stride * 8, 1)
+        stride = max(args.cpu_rows_stride, 1)
         it, dt, nrows, cores = cpu_sample_parallel(v, stride)
         line["cpu_baseline"] = {"value": it / dt / 1e9, "unit": "Giter/s", "cores": cores, "kind": "oracle",
                                 "sample": "%d of %d rows (every %d-th), %d iterations, %.1f s"

@@ -200,10 +200,10 @@ __global__ void __launch_bounds__(512) render_kernel(RenderParams P) {
   __syncthreads();
 
   Lane L;
-  L.zr = L.zi = L.cr = L.ci = 0.0;
-  L.cnt = 0;
-  L.lim = 0;
+  L.zr = L.zi = L.cr = L.ci = L.szr = L.szi = 0.0;
+  L.cnt = L.lim = L.scnt = 0;
   L.live = false;
+  L.pend = false;
   bool has = false;
   bool drained = false;
   uint32_t* optr = nullptr;
@@ -212,7 +212,8 @@ __global__ void __launch_bounds__(512) render_kernel(RenderParams P) {
   EscThr thr{3.99f, 4.01f};
 
   for (;;) {
-    // Retire finished pixels.
+    // Settle provisional escape decisions, then retire finished pixels.
+    resolve(L, r2);
     if (has && !L.live) {
       *optr = L.cnt;
       if (tptr) atomicAdd((unsigned long long*)tptr, (unsigned long long)L.cnt);
@@ -242,6 +243,7 @@ __global__ void __launch_bounds__(512) render_kernel(RenderParams P) {
           L.cnt = 0;
           L.lim = V.iter_max;
           L.live = true;
+          L.pend = false;
           r2 = V.r2;
           thr = V.thr;
           optr = V.out + (size_t)row * V.n + col;

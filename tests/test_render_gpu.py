@@ -237,3 +237,33 @@ def test_sum_counts_and_peak():
     assert int(tot.item()) == sum(range(100000))
     rate, sec = mb.mb_fp64_peak(0)
     assert 1e10 < rate < 1e14 and sec > 0
+
+
+def _next_down(x):
+    return float(np.nextafter(x, 0.0))
+
+
+def _next_up(x):
+    return float(np.nextafter(x, np.inf))
+
+
+@pytest.mark.parametrize("r2", [4.0, 1.12890625, _next_down(1.12890625), _next_up(1.12890625),
+                                  2.6533203125, _next_down(2.6533203125), 36.0, _next_down(36.0),
+                                  _next_down(4.0), _next_up(4.0)])
+def test_escape_band_replay(orc, r2):
+    """Orbits whose |z|^2 hits R2 exactly or one ulp away: the FP32 filter cannot
+    decide them, the provisional run carries on, and the replay must settle the
+    count exactly (c = -2 sits on |z|^2 = 4 at every step; c = 0.5 passes
+    |z|^2 = 1.12890625 and 2.6533203125 exactly; c = 2 passes 4 and 36)."""
+    win, m, n = (-2.0, 2.0, -2.0, 2.0), 4, 8   # c_re in {-2, -1.5, ..., 1.5}, c_im in {2, 1, 0, -1}
+    for it in (1, 2, 3, 5, 17, 1000):
+        want = orc.render(win, m, n, it, r2)
+        for unroll in (4, 16):
+            got = gpu_render(win, m, n, it, r2=r2, sched="fcfs_tiles", tile=8, unroll=unroll)["img"]
+            assert np.array_equal(got, want), (it, unroll)
+    # a window containing c = 0.5, 2 and 1 exactly
+    win2, m2, n2 = (0.0, 4.0, -1.0, 1.0), 2, 8   # c_re = 0, 0.5, ..., 3.5; c_im = 1, 0
+    want = orc.render(win2, m2, n2, 100, r2)
+    got = gpu_render(win2, m2, n2, 100, r2=r2, sched="fcfs_tiles", tile=8)["img"]
+    assert np.array_equal(got, want)
+    assert want[1, 1] == orc.escape(0.5, 0.0, 100, r2)
