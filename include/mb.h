@@ -112,6 +112,28 @@ const char* mb_strerror(int code);
 int mb_render(const mb_window* w, uint32_t m, uint32_t n, uint32_t iter_max, double escape_r2,
               uint32_t* out, const mb_opts* opt);
 
+/* Largest m and n that mb_render_noalloc accepts. */
+#define MB_NOALLOC_MAX_SIDE 16384
+
+/* The paper has no counterpart to this entry point; it exists for callers that
+ * must not allocate device memory.  It renders exactly what mb_render renders
+ * (same arguments, same counts, same options except `workspace`, which must be
+ * NULL), but calls no cudaMalloc / cudaMallocAsync / cudaFree: the temporary
+ * memory it needs sits in one fixed array inside the library's device image
+ * (262,656 bytes, resident on every GPU that loads the library until exit).
+ * Typical callers: code running where the allocator may not be entered (host
+ * callbacks, real-time loops), or processes whose device memory another
+ * framework has reserved up front.
+ *   m, n   each in [1, MB_NOALLOC_MAX_SIDE]; larger sizes return MB_EINVAL.
+ * All calls on a device share the array and it keeps the last call's contents;
+ * every part a render reads is rewritten (the work counter zeroed) on the
+ * stream before the render kernel runs.  Calls whose kernels overlap on the
+ * GPU race on the array: issue them on one stream.  The first call on a device
+ * looks up the array's address (cudaGetSymbolAddress); make it before any
+ * stream capture starts. */
+int mb_render_noalloc(const mb_window* w, uint32_t m, uint32_t n, uint32_t iter_max, double escape_r2,
+                      uint32_t* out, const mb_opts* opt);
+
 /* Bytes of temporary device memory mb_render needs for this size and options
  * (Cx/Cy arrays and work counters), so that a caller can pass opts->workspace. */
 size_t mb_render_workspace_size(uint32_t m, uint32_t n, const mb_opts* opt);

@@ -8,7 +8,7 @@ not load the library; the first call does, and fails loudly if it is missing.
 import ctypes
 
 __all__ = [
-    "mb_version", "mb_strerror", "mb_render", "mb_render_workspace_size", "mb_sum_counts",
+    "mb_version", "mb_strerror", "mb_render", "mb_render_noalloc", "mb_render_workspace_size", "mb_sum_counts",
     "mb_fp64_peak", "mb_device_info", "Window", "MBError",
 ]
 
@@ -93,6 +93,19 @@ def mb_render(window, m, n, iter_max, escape_r2, out, **opts):
     rc = L.lib().mb_render(ctypes.byref(w), int(m), int(n), int(iter_max), float(escape_r2), _ptr(out),
                            ctypes.byref(o))
     _check(rc, "mb_render")
+
+
+def mb_render_noalloc(window, m, n, iter_max, escape_r2, out, **opts):
+    """As mb_render, for callers that must not allocate device memory: the
+    library's fixed scratch array replaces the temporary allocation (m, n each
+    at most 16384; calls on one device share the array, so keep them ordered
+    on one stream)."""
+    L = _L()
+    w = L.mb_window(*map(float, window))
+    o = _opts(**opts)
+    rc = L.lib().mb_render_noalloc(ctypes.byref(w), int(m), int(n), int(iter_max), float(escape_r2), _ptr(out),
+                                   ctypes.byref(o))
+    _check(rc, "mb_render_noalloc")
 
 
 def mb_render_workspace_size(m, n, **opts):

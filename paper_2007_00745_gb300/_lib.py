@@ -50,6 +50,8 @@ def _load():
     L.mb_strerror.argtypes = [i32]
     L.mb_render.argtypes = [ctypes.POINTER(mb_window), u32, u32, u32, f64, vp, ctypes.POINTER(mb_opts)]
     L.mb_render.restype = i32
+    L.mb_render_noalloc.argtypes = [ctypes.POINTER(mb_window), u32, u32, u32, f64, vp, ctypes.POINTER(mb_opts)]
+    L.mb_render_noalloc.restype = i32
     L.mb_render_workspace_size.argtypes = [u32, u32, ctypes.POINTER(mb_opts)]
     L.mb_render_workspace_size.restype = sz
     L.mb_sum_counts.argtypes = [vp, u64, vp, vp]
