@@ -142,6 +142,85 @@ size_t mb_render_workspace_size(uint32_t m, uint32_t n, const mb_opts* opt);
  * i.e. the number of z-updates of a rendered image. */
 int mb_sum_counts(const uint32_t* counts, uint64_t count, uint64_t* total, void* stream);
 
+/* ---- learned tile-cost model (not in the paper: it orders the FCFS queue of
+ * Sec. III-B longest-first and splits heavy tiles; the counts do not change) ----
+ *
+ * Probe: PROBE 8 x 8 samples per tile x tile block; sample (a, b) of tile
+ * (ty, tx) is pixel (ty*T + a*s + s/2, tx*T + b*s + s/2), s = T/8, clamped to
+ * the last row / column.  Features (70 floats per tile, FP32):
+ *   f[8a+b] = log2(1 + probe[a][b]) / log2(1 + iterMax); f[64] = (tx+0.5)/tiles_x;
+ *   f[65] = (ty+0.5)/tiles_y; f[66] = log2(1 + iterMax)/17;
+ *   f[67] = -log10((xmax - xmin)/n)/16; f[68] = mean(f[0..63]);
+ *   f[69] = (samples at iterMax)/64.
+ * Network: 70 -> 64 -> 64 -> 1, ReLU, FP32; flat parameters (MB_MLP_PARAMS)
+ *   W1[64][70], b1[64], W2[64][64], b2[64], W3[64], b3 (row-major W[out][in]).
+ * Target: log2(1 + tile total)/32; loss: mean squared error over the batch.
+ * Adam: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ *   p -= lr (m/(1-b1^t)) / (sqrt(v/(1-b2^t)) + eps).
+ * Order and split (integers after one FP32 rounding): q = 0 if y <= 0 else
+ *   min(trunc(fp32(y*128)), 191); tiles sorted by q descending, ties by tile
+ *   index; c(q) = (2^(q>>2) * {65536,77936,92682,110218}[q&3]) >> 16 (uint64);
+ *   target = max(1, (saturating sum of c) / (4 G)), G = CTAs of the render;
+ *   s = smallest power of two >= ceil(c/target), at most min(16, T/4); the
+ *   tile yields items (tile, k*T/s, T/s), k < s, in sorted order. */
+#define MB_MLP_PARAMS 8769
+#define MB_MLP_FEATURES 70
+
+/* Probe counts (device, tiles*64 uint32) of a view with tile side opts->tile
+ * (>= 16); when image_out (device, m*n) is given the samples are also stored
+ * at their pixels there.  Exact counts, as mb_render. */
+int mb_probe(const mb_window* w, uint32_t m, uint32_t n, uint32_t iter_max, double escape_r2,
+             uint32_t* probe_out, uint32_t* image_out, const mb_opts* opt);
+
+/* Features (device, tiles x 70 floats) from probe counts (device). */
+int mb_tile_features(const uint32_t* probe, const mb_window* w, uint32_t m, uint32_t n, uint32_t iter_max,
+                     uint32_t tile, float* feat, void* stream);
+
+/* Training labels y[t] = log2(1 + totals[t]) / 32 (device arrays), from the
+ * per-tile sums of counts that mb_render records in opts->tile_totals. */
+int mb_tile_targets(const uint64_t* totals, uint32_t ntiles, float* y, void* stream);
+
+/* Predictions y[count] (device) of the network for `count` feature rows (device). */
+int mb_mlp_forward(const float* params, const float* x, uint32_t count, float* y, void* stream);
+
+/* Loss (device float, may be NULL) and gradient (device, MB_MLP_PARAMS floats,
+ * overwritten) of the mean squared error over the rows idx[0..batch) of x
+ * (idx may be NULL: rows 0..batch-1); target is indexed like the rows of x. */
+int mb_mlp_grad(const float* params, const float* x, const uint32_t* idx, uint32_t batch, const float* target,
+                float* grad, float* loss, void* stream);
+
+/* One Adam step, t >= 1 (device arrays of `count` floats). */
+int mb_adam_step(float* params, const float* grad, float* m, float* v, uint32_t count, uint32_t t, float lr,
+                 float beta1, float beta2, float eps, void* stream);
+
+/* Train on the device: `epochs` passes, each over order[e*count .. e*count+count)
+ * (device sample indices, e.g. a seeded shuffle per epoch) in minibatches of
+ * `batch` (the last count % batch samples of an epoch are skipped); Adam with
+ * lr, beta1 0.9, beta2 0.999, eps 1e-8, state in adam_m / adam_v (device,
+ * zeroed by the caller for a fresh start).  epoch_loss (device, may be NULL)
+ * receives the mean minibatch loss of each epoch. */
+int mb_model_train(float* params, float* adam_m, float* adam_v, const float* x, const float* target, uint32_t count,
+                   const uint32_t* order, uint32_t epochs, uint32_t batch, float lr, float* epoch_loss, void* stream);
+
+/* Work list from predicted tile costs (device, ntiles floats): items (device,
+ * capacity entries) and their number (device uint32), per the rule above.
+ * capacity >= 16 * ntiles always suffices; if it is exceeded, *n_items = 0 and
+ * bit 2 is ORed into *status (device, may be NULL). */
+int mb_order_split(const float* cost_pred, uint32_t ntiles, uint32_t tile, uint32_t grid, mb_item* items,
+                   uint32_t capacity, uint32_t* n_items, uint32_t* status, void* stream);
+
+/* The learned pipeline for one view: probe (its samples go straight into
+ * `out`), features, network, order and split, then the FCFS render of the other
+ * pixels over that list.  Same counts as mb_render.  opts->tile >= 16 (default
+ * 64); opts->sched is ignored; opts->trace records the final render's CTAs. */
+int mb_render_learned(const mb_window* w, uint32_t m, uint32_t n, uint32_t iter_max, double escape_r2,
+                      uint32_t* out, const float* params, const mb_opts* opt);
+
+/* Save / load the network parameters (device, MB_MLP_PARAMS floats) as a small
+ * binary file: 8-byte tag "MBMLP701", uint32 count, float32 values. */
+int mb_model_save(const float* params, const char* path);
+int mb_model_load(const char* path, float* params);
+
 /* FP64 issue-rate microbenchmark: runs independent chains of one binary64
  * operation (op: 0 = add, 1 = mul, 2 = fma) on every SM and returns the
  * measured rate in operations per second (a fused multiply-add counts as one

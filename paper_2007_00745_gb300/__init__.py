@@ -133,3 +133,71 @@ def mb_device_info(block=0):
     a, b = ctypes.c_uint32(), ctypes.c_uint32()
     _check(L.lib().mb_device_info(int(block), ctypes.byref(a), ctypes.byref(b)), "mb_device_info")
     return a.value, b.value
+
+
+# ---- learned tile-cost model -------------------------------------------------
+
+MB_MLP_PARAMS = 8769
+MB_MLP_FEATURES = 70
+
+
+def mb_probe(window, m, n, iter_max, escape_r2, probe_out, image_out=None, **opts):
+    """Probe counts (device int32 tensor, tiles*64) of a view; optionally also into image_out."""
+    L = _L()
+    w = L.mb_window(*map(float, window))
+    o = _opts(**opts)
+    _check(L.lib().mb_probe(ctypes.byref(w), int(m), int(n), int(iter_max), float(escape_r2), _ptr(probe_out),
+                            _ptr(image_out), ctypes.byref(o)), "mb_probe")
+
+
+def mb_tile_features(probe, window, m, n, iter_max, tile, feat, stream=None):
+    L = _L()
+    w = L.mb_window(*map(float, window))
+    _check(L.lib().mb_tile_features(_ptr(probe), ctypes.byref(w), int(m), int(n), int(iter_max), int(tile),
+                                    _ptr(feat), _stream(stream)), "mb_tile_features")
+
+
+def mb_tile_targets(totals, ntiles, y, stream=None):
+    _check(_L().lib().mb_tile_targets(_ptr(totals), int(ntiles), _ptr(y), _stream(stream)), "mb_tile_targets")
+
+
+def mb_mlp_forward(params, x, count, y, stream=None):
+    _check(_L().lib().mb_mlp_forward(_ptr(params), _ptr(x), int(count), _ptr(y), _stream(stream)), "mb_mlp_forward")
+
+
+def mb_mlp_grad(params, x, idx, batch, target, grad, loss=None, stream=None):
+    _check(_L().lib().mb_mlp_grad(_ptr(params), _ptr(x), _ptr(idx), int(batch), _ptr(target), _ptr(grad),
+                                  _ptr(loss), _stream(stream)), "mb_mlp_grad")
+
+
+def mb_adam_step(params, grad, m, v, count, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(_L().lib().mb_adam_step(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(count), int(t), float(lr),
+                                   float(beta1), float(beta2), float(eps), _stream(stream)), "mb_adam_step")
+
+
+def mb_model_train(params, adam_m, adam_v, x, target, count, order, epochs, batch, lr=1e-3, epoch_loss=None,
+                   stream=None):
+    _check(_L().lib().mb_model_train(_ptr(params), _ptr(adam_m), _ptr(adam_v), _ptr(x), _ptr(target), int(count),
+                                     _ptr(order), int(epochs), int(batch), float(lr), _ptr(epoch_loss),
+                                     _stream(stream)), "mb_model_train")
+
+
+def mb_order_split(cost_pred, ntiles, tile, grid, items, capacity, n_items, status=None, stream=None):
+    _check(_L().lib().mb_order_split(_ptr(cost_pred), int(ntiles), int(tile), int(grid), _ptr(items),
+                                     int(capacity), _ptr(n_items), _ptr(status), _stream(stream)), "mb_order_split")
+
+
+def mb_render_learned(window, m, n, iter_max, escape_r2, out, params, **opts):
+    L = _L()
+    w = L.mb_window(*map(float, window))
+    o = _opts(**opts)
+    _check(L.lib().mb_render_learned(ctypes.byref(w), int(m), int(n), int(iter_max), float(escape_r2), _ptr(out),
+                                     _ptr(params), ctypes.byref(o)), "mb_render_learned")
+
+
+def mb_model_save(params, path):
+    _check(_L().lib().mb_model_save(_ptr(params), str(path).encode()), "mb_model_save")
+
+
+def mb_model_load(path, params):
+    _check(_L().lib().mb_model_load(str(path).encode(), _ptr(params)), "mb_model_load")

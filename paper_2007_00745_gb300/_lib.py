@@ -60,6 +60,22 @@ def _load():
     L.mb_fp64_peak.restype = i32
     L.mb_device_info.argtypes = [u32, ctypes.POINTER(u32), ctypes.POINTER(u32)]
     L.mb_device_info.restype = i32
+    P = ctypes.POINTER
+    L.mb_probe.argtypes = [P(mb_window), u32, u32, u32, f64, vp, vp, P(mb_opts)]
+    L.mb_tile_features.argtypes = [vp, P(mb_window), u32, u32, u32, u32, vp, vp]
+    L.mb_mlp_forward.argtypes = [vp, vp, u32, vp, vp]
+    L.mb_tile_targets.argtypes = [vp, u32, vp, vp]
+    L.mb_mlp_grad.argtypes = [vp, vp, vp, u32, vp, vp, vp, vp]
+    L.mb_adam_step.argtypes = [vp, vp, vp, vp, u32, u32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                               ctypes.c_float, vp]
+    L.mb_model_train.argtypes = [vp, vp, vp, vp, vp, u32, vp, u32, u32, ctypes.c_float, vp, vp]
+    L.mb_order_split.argtypes = [vp, u32, u32, u32, vp, u32, vp, vp, vp]
+    L.mb_render_learned.argtypes = [P(mb_window), u32, u32, u32, f64, vp, vp, P(mb_opts)]
+    L.mb_model_save.argtypes = [vp, ctypes.c_char_p]
+    L.mb_model_load.argtypes = [ctypes.c_char_p, vp]
+    for name in ("mb_probe", "mb_tile_features", "mb_tile_targets", "mb_mlp_forward", "mb_mlp_grad", "mb_adam_step",
+                 "mb_model_train", "mb_order_split", "mb_render_learned", "mb_model_save", "mb_model_load"):
+        getattr(L, name).restype = i32
     return L
 
 

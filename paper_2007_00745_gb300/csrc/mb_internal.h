@@ -12,7 +12,11 @@ constexpr uint32_t DEFAULT_TILE = 64;
 constexpr uint32_t DEFAULT_BLOCK = 256;
 constexpr uint32_t DEFAULT_UNROLL = 8;
 
-enum ItemKind : int { KIND_ROWS = 0, KIND_RASTER = 1, KIND_LIST = 2, KIND_BATCH = 3 };
+enum ItemKind : int { KIND_ROWS = 0, KIND_RASTER = 1, KIND_LIST = 2, KIND_BATCH = 3, KIND_PROBE = 4 };
+
+// Low-resolution probe: PROBE_SIDE x PROBE_SIDE samples per tile (sample (a, b) at
+// tile-local pixel (a*s + s/2, b*s + s/2), s = tile / PROBE_SIDE, clamped to the image).
+constexpr uint32_t PROBE_SIDE = 8;
 enum SchedKind : int { S_NAIVE = 0, S_ALT = 1, S_FCFS = 2 };
 
 struct RenderParams;

@@ -86,6 +86,7 @@ RenderFn render_fn(int kind, int sched, bool filt, int unroll) {
     return pick_filt<KIND_ROWS, S_FCFS>(filt, unroll);
   }
   if (kind == KIND_RASTER) return pick_filt<KIND_RASTER, S_FCFS>(filt, unroll);
+  if (kind == KIND_PROBE) return pick_filt<KIND_PROBE, S_FCFS>(filt, unroll);
   if (kind == KIND_LIST) return pick_filt<KIND_LIST, S_FCFS>(filt, unroll);
   return pick_filt<KIND_BATCH, S_FCFS>(filt, unroll);
 }

@@ -53,7 +53,10 @@ struct RenderParams {
   const ViewDesc* views;
   const mb_item* items;        // KIND_LIST
   const BatchItem* bitems;     // KIND_BATCH
-  uint32_t n_items;            // rows (KIND_ROWS), tiles (KIND_RASTER) or list length
+  uint32_t n_items;            // rows (KIND_ROWS), tiles (KIND_RASTER / KIND_PROBE) or list length
+  const uint32_t* n_items_dev; // if set, the list length is read from device memory instead
+  uint32_t* probe_out;         // KIND_PROBE: counts, [tile][PROBE_SIDE^2]
+  uint32_t skip_probe;         // tile kinds: 1 = leave the probe's sample pixels alone (already written)
   uint32_t log2_tile;
   uint32_t* counter;           // FCFS work counter (zeroed before launch)
   uint32_t* status;            // error bits (may be null)
@@ -82,14 +85,19 @@ template <int KIND>
 __device__ __forceinline__ uint32_t item_pixels(const RenderParams& P, uint32_t it) {
   if (KIND == KIND_ROWS) return P.views[0].n;
   if (KIND == KIND_RASTER) return 1u << (2 * P.log2_tile);
+  if (KIND == KIND_PROBE) return PROBE_SIDE * PROBE_SIDE;
   if (KIND == KIND_LIST) return (uint32_t)P.items[it].rows << P.log2_tile;
   return (uint32_t)P.bitems[it].rows << P.log2_tile;
 }
 
 // First item of CTA b, and the item after `it`.
+__device__ __forceinline__ uint32_t item_count(const RenderParams& P) {
+  return P.n_items_dev ? *(volatile const uint32_t*)P.n_items_dev : P.n_items;
+}
+
 template <int SCHED>
 __device__ __forceinline__ uint32_t first_item(const RenderParams& P) {
-  uint32_t G = gridDim.x, b = blockIdx.x, N = P.n_items;
+  uint32_t G = gridDim.x, b = blockIdx.x, N = item_count(P);
   if (SCHED == S_NAIVE) {  // S_b = (N/G) b; the last CTA also takes N mod G (Sec. III-A)
     uint32_t per = N / G;
     uint32_t cnt = per + (b == G - 1 ? N % G : 0);
@@ -102,7 +110,7 @@ __device__ __forceinline__ uint32_t first_item(const RenderParams& P) {
 
 template <int SCHED>
 __device__ __forceinline__ uint32_t next_item(const RenderParams& P, uint32_t it) {
-  uint32_t G = gridDim.x, b = blockIdx.x, N = P.n_items;
+  uint32_t G = gridDim.x, b = blockIdx.x, N = item_count(P);
   if (SCHED == S_NAIVE) {
     uint32_t per = N / G;
     uint32_t last = per * (b + 1) + (b == G - 1 ? N % G : 0);
@@ -157,6 +165,16 @@ __device__ __forceinline__ bool decode(const RenderParams& P, uint32_t it, uint3
     tile = 0;
     return true;
   }
+  if (KIND == KIND_PROBE) {
+    const ViewDesc& V = P.views[0];
+    uint32_t ty = it / V.tiles_x, tx = it - ty * V.tiles_x;
+    uint32_t st = (1u << P.log2_tile) / PROBE_SIDE;
+    v = 0;
+    tile = it;
+    row = min((ty << P.log2_tile) + (pix / PROBE_SIDE) * st + st / 2, V.m - 1);
+    col = min((tx << P.log2_tile) + (pix % PROBE_SIDE) * st + st / 2, V.n - 1);
+    return true;
+  }
   uint32_t t, r0;
   if (KIND == KIND_RASTER) {
     v = 0;
@@ -179,9 +197,14 @@ __device__ __forceinline__ bool decode(const RenderParams& P, uint32_t it, uint3
   }
   const ViewDesc& V = P.views[v];
   uint32_t ty = t / V.tiles_x, tx = t - ty * V.tiles_x;
-  row = (ty << P.log2_tile) + r0 + (pix >> P.log2_tile);
-  col = (tx << P.log2_tile) + (pix & ((1u << P.log2_tile) - 1u));
+  uint32_t lr = r0 + (pix >> P.log2_tile), lc = pix & ((1u << P.log2_tile) - 1u);
+  row = (ty << P.log2_tile) + lr;
+  col = (tx << P.log2_tile) + lc;
   tile = t;
+  if (P.skip_probe) {  // the probe kernel already wrote its in-image sample pixels
+    uint32_t st = (1u << P.log2_tile) / PROBE_SIDE;
+    if ((lr % st) == st / 2 && (lc % st) == st / 2) return false;
+  }
   return ty < V.tiles_y && row < V.m && col < V.n;
 }
 
@@ -207,6 +230,7 @@ __global__ void __launch_bounds__(512) render_kernel(RenderParams P) {
   bool has = false;
   bool drained = false;
   uint32_t* optr = nullptr;
+  uint32_t* pptr = nullptr;
   uint64_t* tptr = nullptr;
   double r2 = 4.0;
   EscThr thr{3.99f, 4.01f};
@@ -216,6 +240,7 @@ __global__ void __launch_bounds__(512) render_kernel(RenderParams P) {
     resolve(L, r2);
     if (has && !L.live) {
       *optr = L.cnt;
+      if (KIND == KIND_PROBE && pptr) *pptr = L.cnt;
       if (tptr) atomicAdd((unsigned long long*)tptr, (unsigned long long)L.cnt);
       has = false;
     }
@@ -246,8 +271,14 @@ __global__ void __launch_bounds__(512) render_kernel(RenderParams P) {
           L.pend = false;
           r2 = V.r2;
           thr = V.thr;
-          optr = V.out + (size_t)row * V.n + col;
+          optr = V.out ? V.out + (size_t)row * V.n + col : nullptr;
           tptr = V.totals ? V.totals + tile : nullptr;
+          if (KIND == KIND_PROBE) {  // probe slot, plus the image pixel when an image is given
+            uint32_t* slot = P.probe_out + (size_t)item * (PROBE_SIDE * PROBE_SIDE) + off + rank;
+            pptr = optr ? slot : nullptr;
+            optr = optr ? optr : slot;
+            tptr = nullptr;
+          }
           has = true;
         }
       }

@@ -1,0 +1,75 @@
+"""Training and use of the learned tile-cost model through the C ABI.
+
+Orchestration only: the probe, features, labels, forward, backward, Adam,
+ordering and rendering all run in libmb.so kernels; this module allocates the
+device buffers (torch) and calls the entry points in order.  The network is
+trained on the per-tile totals that the plain renderer records on seeded
+training views (never the view it is later used on).
+"""
+import hashlib
+import json
+import os
+
+import paper_2007_00745_gb300 as mb
+from paper_2007_00745_gb300 import workloads as wl
+
+NF = mb.MB_MLP_FEATURES
+CACHE_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build")
+
+
+def tiles_of(m, n, tile):
+    return (-(-n // tile)) * (-(-m // tile))
+
+
+def build_training_set(views, tile=64, stream=None):
+    """(X [N, 70] float32, y [N] float32) on the device from the given views."""
+    import torch
+    counts = [tiles_of(v.m, v.n, tile) for v in views]
+    N = sum(counts)
+    X = torch.empty((N, NF), dtype=torch.float32, device="cuda")
+    y = torch.empty(N, dtype=torch.float32, device="cuda")
+    off = 0
+    for v, nt in zip(views, counts):
+        probe = torch.empty(nt * 64, dtype=torch.int32, device="cuda")
+        img = torch.empty(v.m * v.n, dtype=torch.int32, device="cuda")
+        tot = torch.zeros(nt, dtype=torch.int64, device="cuda")
+        mb.mb_probe(v.window, v.m, v.n, v.iter_max, v.r2, probe, tile=tile, stream=stream)
+        mb.mb_tile_features(probe, v.window, v.m, v.n, v.iter_max, tile, X.data_ptr() + off * NF * 4, stream=stream)
+        mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, img, tile=tile, tile_totals=tot, stream=stream)
+        mb.mb_tile_targets(tot, nt, y.data_ptr() + off * 4, stream=stream)
+        off += nt
+    return X, y
+
+
+def train(X, y, epochs=40, batch=256, lr=2e-3, seed=wl.SEED + 6, stream=None):
+    """Train from the seeded initial weights; returns (params, per-epoch loss)."""
+    import torch
+    N = X.shape[0]
+    params = torch.from_numpy(wl.mlp_init(seed)).cuda()
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    order = torch.from_numpy(wl.epoch_orders(N, epochs, seed + 1).astype("int32")).cuda()
+    loss = torch.zeros(epochs, dtype=torch.float32, device="cuda")
+    mb.mb_model_train(params, m, v, X, y, N, order, epochs, min(batch, N), lr, loss, stream=stream)
+    return params, loss
+
+
+def default_model(train_views=24, side=1024, tile=64, epochs=40, stream=None, cache=True):
+    """The trained model used by the benchmark: trained on seeded zoom views
+    (training_zoom_views), cached under _build/ keyed by its recipe."""
+    import torch
+    recipe = {"views": train_views, "side": side, "tile": tile, "epochs": epochs, "seed": wl.SEED,
+              "lib": mb.mb_version()}
+    key = hashlib.sha1(json.dumps(recipe, sort_keys=True).encode()).hexdigest()[:12]
+    path = os.path.join(CACHE_DIR, "tile_model_%s.bin" % key)
+    params = torch.empty(mb.MB_MLP_PARAMS, dtype=torch.float32, device="cuda")
+    if cache and os.path.exists(path):
+        mb.mb_model_load(path, params)
+        return params, None
+    X, y = build_training_set(wl.training_zoom_views(train_views, side), tile, stream=stream)
+    params, loss = train(X, y, epochs=epochs, stream=stream)
+    if cache:
+        os.makedirs(CACHE_DIR, exist_ok=True)
+        torch.cuda.synchronize()
+        mb.mb_model_save(params, path)
+    return params, loss

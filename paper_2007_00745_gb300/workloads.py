@@ -130,3 +130,65 @@ def poisson_arrivals(rate_per_s, count, seed=SEED + 5):
         t += -math.log(1.0 - u) / rate_per_s
         out.append(t)
     return out
+
+
+# ---- tile-cost model inputs ------------------------------------------------------
+
+MLP_IN, MLP_HID = 70, 64
+MLP_PARAMS = MLP_HID * MLP_IN + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_HID + 1
+
+
+def _normals(rng, count):
+    """Standard normal draws by the Box-Muller transform of splitmix64 uniforms."""
+    out = []
+    while len(out) < count:
+        u1 = 1.0 - rng.uniform()
+        u2 = rng.uniform()
+        r = math.sqrt(-2.0 * math.log(u1))
+        out.append(r * math.cos(2.0 * math.pi * u2))
+        out.append(r * math.sin(2.0 * math.pi * u2))
+    return out[:count]
+
+
+def mlp_init(seed=SEED + 6):
+    """Initial network parameters (float32, the C ABI's flat layout): He-normal
+    weights, zero hidden biases, output bias 0.5."""
+    import numpy as np
+    rng = SplitMix64(seed)
+    w1 = np.array(_normals(rng, MLP_HID * MLP_IN)) * math.sqrt(2.0 / MLP_IN)
+    w2 = np.array(_normals(rng, MLP_HID * MLP_HID)) * math.sqrt(2.0 / MLP_HID)
+    w3 = np.array(_normals(rng, MLP_HID)) * math.sqrt(1.0 / MLP_HID)
+    p = np.concatenate([w1, np.zeros(MLP_HID), w2, np.zeros(MLP_HID), w3, [0.5]])
+    return p.astype(np.float32)
+
+
+def splitmix_keys(count, seed):
+    """count successive splitmix64 outputs from `seed`, vectorised (uint64)."""
+    import numpy as np
+    with np.errstate(over="ignore"):
+        z = (np.uint64(seed) + np.arange(1, count + 1, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15))
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def epoch_orders(count, epochs, seed=SEED + 7):
+    """One seeded permutation of range(count) per epoch, concatenated (uint32)."""
+    import numpy as np
+    out = [np.argsort(splitmix_keys(count, seed + 1000003 * e), kind="stable") for e in range(epochs)]
+    return np.concatenate(out).astype(np.uint32)
+
+
+def random_features(count, seed=SEED + 8):
+    """Feature-shaped test inputs in [0, 1) (float32, count x 70)."""
+    import numpy as np
+    k = splitmix_keys(count * MLP_IN, seed)
+    return ((k >> np.uint64(40)).astype(np.float64) / float(1 << 24)).astype(np.float32).reshape(count, MLP_IN)
+
+
+def random_costs(count, seed=SEED + 9, lo=-0.05, hi=0.95):
+    """Predicted-cost-shaped test inputs (float32) for the order-and-split kernel."""
+    import numpy as np
+    k = splitmix_keys(count, seed)
+    u = (k >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    return (lo + (hi - lo) * u).astype(np.float32)
