@@ -45,6 +45,7 @@ extern "C" {
 #define MB_EBUSY 5       /* a server queue is full */
 #define MB_ENOTFOUND 6   /* unknown request id */
 #define MB_EDEVICE 7     /* a kernel reported an internal error in its status word */
+#define MB_ECANCELED 8   /* a queued server request was cancelled by mb_serve_destroy */
 
 /* Complex window: c_re spans [xmin, xmax), c_im spans (ymin, ymax]. */
 typedef struct {
@@ -141,6 +142,93 @@ size_t mb_render_workspace_size(uint32_t m, uint32_t n, const mb_opts* opt);
 /* Sum of `count` uint32 values (device) into *total (device uint64, overwritten),
  * i.e. the number of z-updates of a rendered image. */
 int mb_sum_counts(const uint32_t* counts, uint64_t count, uint64_t* total, void* stream);
+
+/* ---- batched mode: many viewports in one persistent launch ----
+ * A view: window, size, iteration budget, R^2 and its own output buffer
+ * (device, m*n uint32).  Each view is rendered exactly as mb_render would. */
+typedef struct {
+  mb_window w;
+  uint32_t m, n, iter_max;
+  double escape_r2;
+  uint32_t* out;
+} mb_view;
+
+/* One-shot batch: pixel maps of all views in one launch, then one FCFS render
+ * over (view, tile) items -- views queued by decreasing iter_max, tiles in
+ * raster order.  1 <= count <= 65535; opts as for mb_render (sched ignored).
+ * Synchronises opts->stream before returning. */
+int mb_render_batch(const mb_view* views, uint32_t count, const mb_opts* opt);
+
+/* A reusable batch: device tables built once, the two launches captured into
+ * a CUDA graph.  mb_batch_plan_launch replays the graph on `stream`
+ * (asynchronous); destroy synchronises the device and frees the plan. */
+typedef struct mb_batch_plan mb_batch_plan;
+int mb_batch_plan_create(const mb_view* views, uint32_t count, const mb_opts* opt, mb_batch_plan** plan);
+int mb_batch_plan_launch(mb_batch_plan* plan, void* stream);
+int mb_batch_plan_info(const mb_batch_plan* plan, uint32_t* n_items, uint32_t* grid, uint64_t* pixels);
+int mb_batch_plan_destroy(mb_batch_plan* plan);
+
+/* Autotuner: times graph replays of the batch (every sample_stride-th view) for
+ * tile in {16, 32, 64} x block in {256, 512} x unroll in {8, 16} and writes the
+ * fastest into *best (other fields copied from base, may be NULL) and its time
+ * into *best_ms.  cache_path (may be NULL): a text file of
+ * "key tile block unroll ms" lines; a hit skips the search. */
+int mb_batch_autotune(const mb_view* views, uint32_t count, const mb_opts* base, uint32_t sample_stride,
+                      const char* cache_path, mb_opts* best, float* best_ms);
+
+/* ---- serving: continuous batching under a device-memory budget ----
+ * A request is one view; the server allocates its counts (m*n uint32) and Cx/Cy
+ * arrays on the device, charging align256(m*n*4) + align256((m+n)*8) bytes to
+ * the budget until the request is released.  Requests that do not fit yet wait
+ * in a FIFO of at most queue_limit entries.  A worker thread keeps two rounds
+ * in flight on two streams; each round is one FCFS render over the next tiles
+ * of every admitted request (oldest first, at most 8 x grid tiles), so requests
+ * that arrive while others run join the next round and share the GPU.  Counts
+ * are exactly those of mb_render.  Timestamps are host steady-clock ns. */
+typedef struct {
+  mb_window w;
+  uint32_t m, n, iter_max;
+  double escape_r2;
+} mb_request;
+
+typedef struct {
+  uint64_t submit_ns, admit_ns, start_ns, done_ns;
+  uint64_t bytes;
+  int status;
+} mb_req_stats;
+
+typedef struct {
+  uint64_t submitted, admitted, completed, rejected, rounds;
+  uint64_t bytes_in_use, peak_bytes;
+  uint32_t queued;
+} mb_serve_counters;
+
+typedef struct mb_server mb_server;
+
+/* opts: tile (default 32), block (512), unroll (16), grid; other fields ignored.
+ * queue_limit 0 = 1024. */
+int mb_serve_create(size_t mem_budget_bytes, uint32_t queue_limit, const mb_opts* opt, mb_server** s);
+/* MB_ENOMEM if the request alone exceeds the budget, MB_EBUSY if the queue is full. */
+int mb_serve_submit(mb_server* s, const mb_request* rq, uint64_t* id);
+/* Waits up to timeout_ms for completion: MB_OK, MB_ETIMEDOUT, MB_ENOTFOUND, or
+ * the request's failure code (MB_ECANCELED, MB_ECUDA, ...). */
+int mb_serve_wait(mb_server* s, uint64_t id, uint32_t timeout_ms, mb_req_stats* st);
+/* Device pointer to a completed request's counts, valid until mb_serve_release. */
+int mb_serve_result(mb_server* s, uint64_t id, uint32_t** dev_out);
+/* Copies the first `count` counts of a completed request into dst (device or
+ * host memory; unified addressing picks the direction) on `stream`, and waits
+ * for the copy.  Must not overlap with mb_serve_release of the same id. */
+int mb_serve_read(mb_server* s, uint64_t id, uint32_t* dst, uint64_t count, void* stream);
+/* Frees a completed or failed request's device memory and budget (MB_EBUSY while it runs). */
+int mb_serve_release(mb_server* s, uint64_t id);
+int mb_serve_counters_get(mb_server* s, mb_serve_counters* c);
+/* Marks the server failed with `code` (fault injection for tests, or an
+ * application's own abort): pending requests fail with it, new submits return it. */
+int mb_serve_fail(mb_server* s, int code);
+/* Cancels queued requests (MB_ECANCELED), lets admitted ones finish, joins the
+ * worker, returns every thread blocked in mb_serve_wait, then frees all device
+ * memory.  No other call on `s` may start once destroy has begun. */
+int mb_serve_destroy(mb_server* s);
 
 /* ---- learned tile-cost model (not in the paper: it orders the FCFS queue of
  * Sec. III-B longest-first and splits heavy tiles; the counts do not change) ----

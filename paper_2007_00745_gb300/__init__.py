@@ -201,3 +201,135 @@ def mb_model_save(params, path):
 
 def mb_model_load(path, params):
     _check(_L().lib().mb_model_load(str(path).encode(), _ptr(params)), "mb_model_load")
+
+
+# ---- batched mode ------------------------------------------------------------------
+
+def _views(views, outs):
+    L = _L()
+    arr = (L.mb_view * len(views))()
+    for k, (v, o) in enumerate(zip(views, outs)):
+        arr[k].w = L.mb_window(*map(float, v[0]))
+        arr[k].m, arr[k].n, arr[k].iter_max = int(v[1]), int(v[2]), int(v[3])
+        arr[k].escape_r2 = float(v[4])
+        arr[k].out = _ptr(o)
+    return arr
+
+
+def mb_render_batch(views, outs, **opts):
+    """Render every view (window, m, n, iter_max, r2) into its device tensor in outs."""
+    L = _L()
+    arr = _views(views, outs)
+    o = _opts(**opts)
+    _check(L.lib().mb_render_batch(arr, len(views), ctypes.byref(o)), "mb_render_batch")
+
+
+class BatchPlan:
+    """mb_batch_plan_*: device tables built once, launches captured in a CUDA graph."""
+
+    def __init__(self, views, outs, **opts):
+        L = _L()
+        self._arr = _views(views, outs)
+        self._opts = _opts(**opts)
+        self._h = ctypes.c_void_p()
+        _check(L.lib().mb_batch_plan_create(self._arr, len(views), ctypes.byref(self._opts), ctypes.byref(self._h)),
+               "mb_batch_plan_create")
+
+    def launch(self, stream=None):
+        _check(_L().lib().mb_batch_plan_launch(self._h, _stream(stream)), "mb_batch_plan_launch")
+
+    def info(self):
+        a, b, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64()
+        _check(_L().lib().mb_batch_plan_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "mb_batch_plan_info")
+        return {"items": a.value, "grid": b.value, "pixels": c.value}
+
+    def destroy(self):
+        if self._h:
+            _check(_L().lib().mb_batch_plan_destroy(self._h), "mb_batch_plan_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def mb_batch_autotune(views, outs, sample_stride=1, cache_path=None, **base):
+    """Fastest (tile, block, unroll) for the batch and its time in ms."""
+    L = _L()
+    arr = _views(views, outs)
+    b = _opts(**base)
+    best = L.mb_opts()
+    ms = ctypes.c_float()
+    _check(L.lib().mb_batch_autotune(arr, len(views), ctypes.byref(b), int(sample_stride),
+                                     cache_path.encode() if cache_path else None, ctypes.byref(best),
+                                     ctypes.byref(ms)), "mb_batch_autotune")
+    return {"tile": best.tile, "block": best.block, "unroll": best.unroll}, ms.value
+
+
+# ---- serving -------------------------------------------------------------------------
+
+MB_OK, MB_EINVAL, MB_ENOMEM, MB_ECUDA, MB_ETIMEDOUT, MB_EBUSY, MB_ENOTFOUND, MB_EDEVICE, MB_ECANCELED = range(9)
+
+
+class Server:
+    """mb_serve_*: continuous-batching render server under a device-memory budget."""
+
+    def __init__(self, budget_bytes, queue_limit=0, **opts):
+        L = _L()
+        o = _opts(**opts)
+        self._h = ctypes.c_void_p()
+        _check(L.lib().mb_serve_create(int(budget_bytes), int(queue_limit), ctypes.byref(o), ctypes.byref(self._h)),
+               "mb_serve_create")
+
+    def submit(self, view):
+        """Submit (window, m, n, iter_max, r2); returns the request id."""
+        L = _L()
+        r = L.mb_request(L.mb_window(*map(float, view[0])), int(view[1]), int(view[2]), int(view[3]),
+                         float(view[4]))
+        rid = ctypes.c_uint64()
+        _check(L.lib().mb_serve_submit(self._h, ctypes.byref(r), ctypes.byref(rid)), "mb_serve_submit")
+        return rid.value
+
+    def wait(self, rid, timeout_ms=60000):
+        """(return code, stats dict); does not raise on timeout or request failure."""
+        L = _L()
+        st = L.mb_req_stats()
+        rc = L.lib().mb_serve_wait(self._h, int(rid), int(timeout_ms), ctypes.byref(st))
+        return rc, {k: getattr(st, k) for k, _ in L.mb_req_stats._fields_}
+
+    def result(self, rid):
+        """Device address of the counts (valid until release)."""
+        p = ctypes.c_void_p()
+        _check(_L().lib().mb_serve_result(self._h, int(rid), ctypes.byref(p)), "mb_serve_result")
+        return p.value
+
+    def read(self, rid, dst, count=None, stream=None):
+        """Copy the counts into dst (device or pinned/pageable host tensor)."""
+        n = dst.numel() if count is None else int(count)
+        _check(_L().lib().mb_serve_read(self._h, int(rid), _ptr(dst), n, _stream(stream)), "mb_serve_read")
+
+    def release(self, rid):
+        _check(_L().lib().mb_serve_release(self._h, int(rid)), "mb_serve_release")
+
+    def counters(self):
+        L = _L()
+        c = L.mb_serve_counters()
+        _check(L.lib().mb_serve_counters_get(self._h, ctypes.byref(c)), "mb_serve_counters_get")
+        return {k: getattr(c, k) for k, _ in L.mb_serve_counters._fields_}
+
+    def fail(self, code):
+        _check(_L().lib().mb_serve_fail(self._h, int(code)), "mb_serve_fail")
+
+    def destroy(self):
+        if self._h:
+            _check(_L().lib().mb_serve_destroy(self._h), "mb_serve_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmb.so")
 u8, u16, u32, u64 = ctypes.c_uint8, ctypes.c_uint16, ctypes.c_uint32, ctypes.c_uint64
 i32, f64, vp, sz = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
 
-MB_OK, MB_EINVAL, MB_ENOMEM, MB_ECUDA, MB_ETIMEDOUT, MB_EBUSY, MB_ENOTFOUND, MB_EDEVICE = range(8)
+MB_OK, MB_EINVAL, MB_ENOMEM, MB_ECUDA, MB_ETIMEDOUT, MB_EBUSY, MB_ENOTFOUND, MB_EDEVICE, MB_ECANCELED = range(9)
 MB_SCHED_NAIVE, MB_SCHED_ALTERNATING, MB_SCHED_FCFS_ROWS, MB_SCHED_FCFS_TILES, MB_SCHED_FCFS_ITEMS = range(5)
 
 
@@ -33,6 +33,24 @@ class mb_opts(ctypes.Structure):
     _fields_ = [("sched", i32), ("tile", u32), ("grid", u32), ("block", u32), ("unroll", u32),
                 ("stream", vp), ("items", vp), ("n_items", u32), ("tile_totals", vp), ("trace", vp), ("trace_len", u32),
                 ("status", vp), ("workspace", vp), ("workspace_bytes", sz)]
+
+
+class mb_view(ctypes.Structure):
+    _fields_ = [("w", mb_window), ("m", u32), ("n", u32), ("iter_max", u32), ("escape_r2", f64), ("out", vp)]
+
+
+class mb_request(ctypes.Structure):
+    _fields_ = [("w", mb_window), ("m", u32), ("n", u32), ("iter_max", u32), ("escape_r2", f64)]
+
+
+class mb_req_stats(ctypes.Structure):
+    _fields_ = [("submit_ns", u64), ("admit_ns", u64), ("start_ns", u64), ("done_ns", u64), ("bytes", u64),
+                ("status", i32)]
+
+
+class mb_serve_counters(ctypes.Structure):
+    _fields_ = [("submitted", u64), ("admitted", u64), ("completed", u64), ("rejected", u64), ("rounds", u64),
+                ("bytes_in_use", u64), ("peak_bytes", u64), ("queued", u32)]
 
 
 class MBError(RuntimeError):
@@ -73,6 +91,28 @@ def _load():
     L.mb_render_learned.argtypes = [P(mb_window), u32, u32, u32, f64, vp, vp, P(mb_opts)]
     L.mb_model_save.argtypes = [vp, ctypes.c_char_p]
     L.mb_model_load.argtypes = [ctypes.c_char_p, vp]
+    L.mb_render_batch.argtypes = [P(mb_view), u32, P(mb_opts)]
+    L.mb_batch_plan_create.argtypes = [P(mb_view), u32, P(mb_opts), P(vp)]
+    L.mb_batch_plan_launch.argtypes = [vp, vp]
+    L.mb_batch_plan_info.argtypes = [vp, P(u32), P(u32), P(u64)]
+    L.mb_batch_plan_destroy.argtypes = [vp]
+    L.mb_batch_autotune.argtypes = [P(mb_view), u32, P(mb_opts), u32, ctypes.c_char_p, P(mb_opts),
+                                    P(ctypes.c_float)]
+    L.mb_serve_create.argtypes = [sz, u32, P(mb_opts), P(vp)]
+    L.mb_serve_submit.argtypes = [vp, P(mb_request), P(u64)]
+    L.mb_serve_wait.argtypes = [vp, u64, u32, P(mb_req_stats)]
+    L.mb_serve_result.argtypes = [vp, u64, P(vp)]
+    L.mb_serve_release.argtypes = [vp, u64]
+    L.mb_serve_read.argtypes = [vp, u64, vp, u64, vp]
+    L.mb_serve_counters_get.argtypes = [vp, P(mb_serve_counters)]
+    L.mb_serve_fail.argtypes = [vp, i32]
+    L.mb_serve_destroy.argtypes = [vp]
+    for name in ("mb_serve_create", "mb_serve_submit", "mb_serve_wait", "mb_serve_result", "mb_serve_release", "mb_serve_read",
+                 "mb_serve_counters_get", "mb_serve_fail", "mb_serve_destroy"):
+        getattr(L, name).restype = i32
+    for name in ("mb_render_batch", "mb_batch_plan_create", "mb_batch_plan_launch", "mb_batch_plan_info",
+                 "mb_batch_plan_destroy", "mb_batch_autotune"):
+        getattr(L, name).restype = i32
     for name in ("mb_probe", "mb_tile_features", "mb_tile_targets", "mb_mlp_forward", "mb_mlp_grad", "mb_adam_step",
                  "mb_model_train", "mb_order_split", "mb_render_learned", "mb_model_save", "mb_model_load"):
         getattr(L, name).restype = i32

@@ -63,6 +63,7 @@ extern "C" const char* mb_strerror(int code) {
     case MB_EBUSY: return "busy";
     case MB_ENOTFOUND: return "not found";
     case MB_EDEVICE: return "device-side error";
+    case MB_ECANCELED: return "cancelled";
     default: return "unknown error";
   }
 }
