@@ -94,6 +94,8 @@ typedef struct {
   uint32_t* status;          /* device, optional: kernels OR error bits into it (0 = fine) */
   void* workspace;           /* device, optional: temporary memory, >= mb_render_workspace_size() bytes, 256-byte aligned */
   size_t workspace_bytes;
+  void* ev_start;            /* cudaEvent_t, optional: recorded on the stream right before the main render kernel */
+  void* ev_stop;             /* cudaEvent_t, optional: recorded right after it (to time that kernel alone) */
 } mb_opts;
 
 /* Library version string. */

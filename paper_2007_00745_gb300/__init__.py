@@ -48,7 +48,8 @@ def _stream(stream):
 
 
 def _opts(sched="fcfs_tiles", tile=0, grid=0, block=0, unroll=0, stream=None, items=None, n_items=0,
-          tile_totals=None, trace=None, trace_len=0, status=None, workspace=None, workspace_bytes=0):
+          tile_totals=None, trace=None, trace_len=0, status=None, workspace=None, workspace_bytes=0,
+          events=None):
     L = _L()
     o = L.mb_opts()
     o.sched = SCHEDS[sched] if isinstance(sched, str) else int(sched)
@@ -61,6 +62,16 @@ def _opts(sched="fcfs_tiles", tile=0, grid=0, block=0, unroll=0, stream=None, it
     o.trace_len = int(trace_len if trace_len else (trace.numel() * trace.element_size() // 24
                                                    if trace is not None and hasattr(trace, "numel") else 0))
     o.status = _ptr(status)
+    if events is not None:   # (start, stop) torch.cuda.Event pair recorded around the main render kernel
+        handles = []
+        for ev in events:
+            if hasattr(ev, "cuda_event"):
+                if not ev.cuda_event:   # torch creates the CUDA event on its first record
+                    ev.record()
+                handles.append(ev.cuda_event)
+            else:
+                handles.append(int(ev))
+        o.ev_start, o.ev_stop = handles
     o.workspace = _ptr(workspace)
     o.workspace_bytes = int(workspace_bytes if workspace_bytes else
                             (workspace.numel() * workspace.element_size() if workspace is not None
@@ -118,6 +129,11 @@ def mb_sum_counts(counts, total, stream=None):
     """Sum of the uint32 counts in device tensor `counts` into device int64 tensor `total`."""
     _check(_L().lib().mb_sum_counts(_ptr(counts), int(counts.numel()), _ptr(total), _stream(stream)),
            "mb_sum_counts")
+
+
+def mb_sum_counts_ptr(counts_ptr, count, total, stream=None):
+    """mb_sum_counts on a raw device address (e.g. a served request's counts)."""
+    _check(_L().lib().mb_sum_counts(int(counts_ptr), int(count), _ptr(total), _stream(stream)), "mb_sum_counts")
 
 
 def mb_fp64_peak(op=0):

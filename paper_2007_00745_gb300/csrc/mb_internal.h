@@ -29,6 +29,9 @@ int check_view(const mb_window* w, uint32_t m, uint32_t n, double r2, const void
 int check_opts(const mb_opts* o, uint32_t* log2_tile);
 RenderFn render_fn(int kind, int sched, bool filt, int unroll);
 int launch_render(const RenderFn fn, const RenderParams& P, uint32_t grid, uint32_t block, cudaStream_t st);
+// launch_render with the caller's optional timing events around it (opts->ev_start / ev_stop)
+int launch_render_timed(const RenderFn fn, const RenderParams& P, uint32_t grid, uint32_t block, cudaStream_t st,
+                        const mb_opts* opt);
 uint32_t default_grid(RenderFn fn, uint32_t block);
 int sm_count();
 int resident_ctas(const void* fn, int block);

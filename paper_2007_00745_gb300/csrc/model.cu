@@ -678,7 +678,7 @@ extern "C" int mb_render_learned(const mb_window* w, uint32_t m, uint32_t n, uin
     PR.skip_probe = 1;
     PR.trace = opt ? opt->trace : nullptr;
     PR.trace_len = opt && opt->trace ? opt->trace_len : 0;
-    rc = launch_render(frender, PR, grid, block, st);
+    rc = launch_render_timed(frender, PR, grid, block, st, opt);
   }
   cudaFreeAsync(ws, st);
   return rc;

@@ -138,6 +138,15 @@ int launch_render(const RenderFn fn, const RenderParams& P, uint32_t grid, uint3
   return cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
 }
 
+int launch_render_timed(const RenderFn fn, const RenderParams& P, uint32_t grid, uint32_t block, cudaStream_t st,
+                        const mb_opts* opt) {
+  if (opt && opt->ev_start && cudaEventRecord((cudaEvent_t)opt->ev_start, st) != cudaSuccess) return MB_ECUDA;
+  int rc = launch_render(fn, P, grid, block, st);
+  if (rc == MB_OK && opt && opt->ev_stop && cudaEventRecord((cudaEvent_t)opt->ev_stop, st) != cudaSuccess)
+    rc = MB_ECUDA;
+  return rc;
+}
+
 uint32_t default_grid(RenderFn fn, uint32_t block) {
   return (uint32_t)(sm_count() * resident_ctas((const void*)fn, (int)block));
 }
@@ -221,7 +230,7 @@ extern "C" int mb_render(const mb_window* w, uint32_t m, uint32_t n, uint32_t it
   if (map_blocks > 1024) map_blocks = 1024;
   pixel_map_single_kernel<<<map_blocks, 256, 0, st>>>(V, (ViewDesc*)(ws + lay.view), P.counter);
   rc = cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
-  if (rc == MB_OK) rc = launch_render(fn, P, grid, block, st);
+  if (rc == MB_OK) rc = launch_render_timed(fn, P, grid, block, st, opt);
   if (owned) cudaFreeAsync(ws, st);
   return rc;
 }
