@@ -91,9 +91,14 @@ typedef struct {
   uint64_t* tile_totals;     /* device, optional: += sum of counts per tile (row-major tiles); caller zeroes it */
   mb_cta_trace* trace;       /* device, optional: one record per CTA, for CTAs below trace_len */
   uint32_t trace_len;        /* records available at `trace` */
-  uint32_t* status;          /* device, optional: kernels OR error bits into it (0 = fine) */
+  uint32_t* status;          /* device, optional: kernels OR error bits into it (0 = fine; 1 = a bounded wait
+                                ran out, 2 = an item outside its tile, 4 = max_seconds reached) */
   void* workspace;           /* device, optional: temporary memory, >= mb_render_workspace_size() bytes, 256-byte aligned */
   size_t workspace_bytes;
+  uint32_t max_seconds;      /* 0 = no limit; else each CTA of the main render stops after running this long
+                                and ORs 4 into *status (a guard for interactive use; the image is then incomplete) */
+  uint32_t fp64_products;    /* 1 = form the three products of a step on the FP64 pipe (MB_SCHED_FCFS_TILES
+                                only; a measured baseline), 0 = exactly on the integer pipes (default) */
   void* ev_start;            /* cudaEvent_t, optional: recorded on the stream right before the main render kernel */
   void* ev_stop;             /* cudaEvent_t, optional: recorded right after it (to time that kernel alone) */
 } mb_opts;
@@ -317,6 +322,14 @@ int mb_model_load(const char* path, float* params);
  * operation) and the elapsed kernel time.  Synchronous.  This rate is the
  * denominator of "% of FP64 peak". */
 int mb_fp64_peak(int op, double* ops_per_s, double* seconds);
+
+/* Self-test of the integer-pipe products used by every render (not in the
+ * paper): for i < n, sq[i] = RN(a[i]*a[i]), pr[i] = RN((2*a[i])*b[i]) as the
+ * kernels form them, and ok[i] = 1 when both operands are in the range where
+ * those results are exact (exponents in [2^-510, 2^511)); outside it the
+ * kernels replay the step on the FP64 pipe instead.  Device arrays. */
+int mb_selftest_products(const double* a, const double* b, uint64_t n, double* sq, double* pr, uint8_t* ok,
+                         void* stream);
 
 /* Number of SMs and resident CTAs per SM the render kernel gets at `block` threads. */
 int mb_device_info(uint32_t block, uint32_t* sms, uint32_t* ctas_per_sm);

@@ -49,7 +49,7 @@ def _stream(stream):
 
 def _opts(sched="fcfs_tiles", tile=0, grid=0, block=0, unroll=0, stream=None, items=None, n_items=0,
           tile_totals=None, trace=None, trace_len=0, status=None, workspace=None, workspace_bytes=0,
-          events=None):
+          events=None, fp64_products=0, max_seconds=300):
     L = _L()
     o = L.mb_opts()
     o.sched = SCHEDS[sched] if isinstance(sched, str) else int(sched)
@@ -62,6 +62,8 @@ def _opts(sched="fcfs_tiles", tile=0, grid=0, block=0, unroll=0, stream=None, it
     o.trace_len = int(trace_len if trace_len else (trace.numel() * trace.element_size() // 24
                                                    if trace is not None and hasattr(trace, "numel") else 0))
     o.status = _ptr(status)
+    o.fp64_products = int(fp64_products)
+    o.max_seconds = int(max_seconds)
     if events is not None:   # (start, stop) torch.cuda.Event pair recorded around the main render kernel
         handles = []
         for ev in events:
@@ -142,6 +144,12 @@ def mb_fp64_peak(op=0):
     r, s = ctypes.c_double(), ctypes.c_double()
     _check(L.lib().mb_fp64_peak(int(op), ctypes.byref(r), ctypes.byref(s)), "mb_fp64_peak")
     return r.value, s.value
+
+
+def mb_selftest_products(a, b, sq, pr, ok, stream=None):
+    """Integer-pipe products of the render kernels on device arrays (see include/mb.h)."""
+    _check(_L().lib().mb_selftest_products(_ptr(a), _ptr(b), int(a.numel()), _ptr(sq), _ptr(pr), _ptr(ok),
+                                           _stream(stream)), "mb_selftest_products")
 
 
 def mb_device_info(block=0):

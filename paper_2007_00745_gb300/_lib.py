@@ -32,7 +32,8 @@ class mb_cta_trace(ctypes.Structure):
 class mb_opts(ctypes.Structure):
     _fields_ = [("sched", i32), ("tile", u32), ("grid", u32), ("block", u32), ("unroll", u32),
                 ("stream", vp), ("items", vp), ("n_items", u32), ("tile_totals", vp), ("trace", vp), ("trace_len", u32),
-                ("status", vp), ("workspace", vp), ("workspace_bytes", sz), ("ev_start", vp), ("ev_stop", vp)]
+                ("status", vp), ("workspace", vp), ("workspace_bytes", sz), ("max_seconds", u32), ("fp64_products", u32),
+                ("ev_start", vp), ("ev_stop", vp)]
 
 
 class mb_view(ctypes.Structure):
@@ -77,6 +78,8 @@ def _load():
     L.mb_fp64_peak.argtypes = [i32, ctypes.POINTER(f64), ctypes.POINTER(f64)]
     L.mb_fp64_peak.restype = i32
     L.mb_device_info.argtypes = [u32, ctypes.POINTER(u32), ctypes.POINTER(u32)]
+    L.mb_selftest_products.argtypes = [vp, vp, u64, vp, vp, vp, vp]
+    L.mb_selftest_products.restype = i32
     L.mb_device_info.restype = i32
     P = ctypes.POINTER
     L.mb_probe.argtypes = [P(mb_window), u32, u32, u32, f64, vp, vp, P(mb_opts)]

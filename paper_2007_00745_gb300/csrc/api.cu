@@ -47,9 +47,28 @@ __global__ void fp64_peak_kernel(double* sink, double y, double z, int iters) {
   if (s == 12345.678) sink[blockIdx.x] = s;  // keeps the chains alive
 }
 
+__global__ void selftest_products_kernel(const double* __restrict__ a, const double* __restrict__ b, uint64_t n,
+                                         double* __restrict__ sq, double* __restrict__ pr, uint8_t* __restrict__ ok) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    sq[i] = emul_sqr(a[i]);
+    pr[i] = emul_mul(a[i], b[i], 1);
+    ok[i] = (uint8_t)(emul_ok(a[i]) && emul_ok(b[i]));
+  }
+}
+
 }  // namespace mb
 
 using namespace mb;
+
+extern "C" int mb_selftest_products(const double* a, const double* b, uint64_t n, double* sq, double* pr,
+                                    uint8_t* ok, void* stream) {
+  if (!a || !b || !sq || !pr || !ok) return MB_EINVAL;
+  if (n == 0) return MB_OK;
+  uint64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  selftest_products_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(a, b, n, sq, pr, ok);
+  return cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
+}
 
 extern "C" const char* mb_version(void) { return "mb 0.1.0 (sm_103a)"; }
 

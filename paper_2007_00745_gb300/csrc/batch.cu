@@ -172,6 +172,7 @@ static int batch_enqueue(mb_batch_plan* P, cudaStream_t st, const mb_opts* opt) 
   R.status = P->status;
   R.trace = opt ? opt->trace : nullptr;
   R.trace_len = opt && opt->trace ? opt->trace_len : 0;
+  R.deadline_ns = opt_deadline_ns(opt);
   return launch_render_timed(P->fn, R, P->grid, P->block, st, opt);
 }
 

@@ -7,23 +7,23 @@
 //
 // GB300's FP64 pipe delivers about 1.7 lanes per clock per SM (measured),
 // against 64-128 for the integer and FP32 pipes, and the pipes run
-// concurrently.  So a step issues only six FP64 operations (three multiplies,
-// three adds) and does the rest exactly on the other pipes, without a branch:
-//  * 2*zr is formed by integer operations on its bit pattern (exponent + 1 for
-//    normal numbers, a one-bit shift for zeros and subnormals, infinity past
-//    the largest finite exponent) -- exactly the value the FP64 multiply by two
-//    would give -- and (2*zr)*zi is then one FP64 multiply, as in the method.
+// concurrently.  A step therefore keeps only the three additions on the FP64
+// pipe and does everything else exactly on the other pipes, without a branch:
+//  * the three products zr*zr, zi*zi and (2*zr)*zi are formed exactly on the
+//    integer pipes (emul_mul / emul_sqr: 53 x 53-bit mantissa products from
+//    four or three 32 x 32 -> 64-bit multiplies, then one normalisation and
+//    round-to-nearest-even), valid whenever zr and zi are normal numbers with
+//    exponents in [2^-510, 2^511) -- then every product is a normal number;
 //  * the escape test RN(zr2 + zi2) > R2 is decided from FP32 truncations of
 //    zr2 and zi2 whenever their sum is more than 2^-16 (relative) away from R2;
-//    the error bounds in filter_sure() make that decision exact.  Within the
-//    band the lane carries on as if it had not escaped and saves the state of
-//    that step; resolve() later replays the saved steps with the literal FP64
-//    add and compare and corrects the count if the lane had in fact escaped.
-// Measured on GB300: any branch or predicated FP64 instruction inside the step
-// (even one that is almost never taken) costs about a quarter of the
-// throughput, because the warp then waits for the FP64 results before it can
-// issue the next step's independent work; the deferred replay keeps the step
-// straight-line.
+//    the error bounds in filter_sure() make that decision exact.
+// A step that meets neither condition (a zero, a tiny or huge component, or a
+// sum within the band) marks the lane pending and carries on; every block of
+// steps starts from a saved copy of the lane's state, and resolve() replays a
+// pending lane's block with the literal FP64 operations, restoring the exact
+// state and count.  Measured on GB300: a branch or predicated FP64 instruction
+// inside the step costs about a quarter of the throughput, so the step stays
+// straight-line and all exceptions go through the replay.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -80,6 +80,60 @@ __device__ __forceinline__ double twice(double x) {
   return __hiloint2double(rh, rl);
 }
 
+// Exponent fields in [513, 1533] (values in [2^-510, 2^511)): for zr and zi in
+// this range the three products of a step are normal binary64 numbers.
+constexpr uint32_t EMUL_E_LO = 513, EMUL_E_SPAN = 1533 - 513;
+
+__device__ __forceinline__ bool emul_ok(double x) {
+  uint32_t e = ((uint32_t)__double2hiint(x) >> 20) & 0x7FFu;
+  return e - EMUL_E_LO <= EMUL_E_SPAN;
+}
+
+// Round-to-nearest-even of the 106-bit mantissa product P = hi*2^64 + m*2^32 + l
+// (2^104 <= P < 2^106) to 53 bits, packed with biased exponent E0 + (P >= 2^105).
+__device__ __forceinline__ double emul_pack(uint64_t hi, uint32_t m, uint32_t l, int E0, uint32_t sign) {
+  uint32_t top = (uint32_t)(hi >> 41);
+  uint32_t s = 1u - top;
+  uint64_t W = (hi << (22 + s)) | (uint64_t)(m >> (10 - s));
+  uint64_t M = W >> 11;
+  uint32_t rnd = (uint32_t)(W >> 10) & 1u;
+  bool sticky = ((uint32_t)W & 0x3FFu) != 0u || (m << (22 + s)) != 0u || l != 0u;
+  M += (rnd && (sticky || (M & 1u))) ? 1u : 0u;
+  uint64_t bits = ((uint64_t)(uint32_t)(E0 + (int)top - 1) << 52) + M;
+  return __hiloint2double((int)((uint32_t)(bits >> 32) | sign), (int)(uint32_t)bits);
+}
+
+// RN(a*b) * 2^e_add, exact when a and b pass emul_ok() (so that the result is
+// normal and 2^e_add, e_add in {0, 1}, does not overflow it).
+__device__ __forceinline__ double emul_mul(double a, double b, int e_add) {
+  uint32_t ah = (uint32_t)__double2hiint(a), al = (uint32_t)__double2loint(a);
+  uint32_t bh = (uint32_t)__double2hiint(b), bl = (uint32_t)__double2loint(b);
+  uint32_t A = (ah & 0xFFFFFu) | 0x100000u, C = (bh & 0xFFFFFu) | 0x100000u;
+  uint64_t bd = (uint64_t)al * bl;
+  uint64_t mid = (uint64_t)A * bl + (bd >> 32);
+  mid += (uint64_t)al * C;
+  uint64_t hi = (uint64_t)A * C + (mid >> 32);
+  int E0 = (int)((ah >> 20) & 0x7FFu) + (int)((bh >> 20) & 0x7FFu) - 1023 + e_add;
+  return emul_pack(hi, (uint32_t)mid, (uint32_t)bd, E0, (ah ^ bh) & 0x80000000u);
+}
+
+// RN(a*a), exact when a passes emul_ok().
+__device__ __forceinline__ double emul_sqr(double a) {
+  uint32_t ah = (uint32_t)__double2hiint(a), al = (uint32_t)__double2loint(a);
+  uint32_t A = (ah & 0xFFFFFu) | 0x100000u;
+  uint64_t bd = (uint64_t)al * al;
+  uint64_t mid = (uint64_t)(A << 1) * al + (bd >> 32);
+  uint64_t hi = (uint64_t)A * A + (mid >> 32);
+  int E0 = 2 * (int)((ah >> 20) & 0x7FFu) - 1023;
+  return emul_pack(hi, (uint32_t)mid, (uint32_t)bd, E0, 0u);
+}
+
+// RN(0 + x): the first step from z = 0 gives z = (RN(0 + cr), RN(0 + ci)), which
+// is c itself except that -0 becomes +0.
+__device__ __forceinline__ double plus_zero(double x) {
+  return __double_as_longlong(x) == (long long)0x8000000000000000ull ? 0.0 : x;
+}
+
 // Binary64 operations that the compiler may not hoist out of the rare replay
 // branch in resolve().
 __device__ __forceinline__ double dadd_branch(double a, double b) {
@@ -101,34 +155,61 @@ __device__ __forceinline__ double dmul_branch(double a, double b) {
 // State of one lane's pixel.
 struct Lane {
   double zr, zi, cr, ci;
-  double szr, szi;  // state at the start of the first undecided escape test since the last resolve()
+  double szr, szi;  // state at the start of the current block of steps
   uint32_t cnt;     // z-updates made so far
   uint32_t lim;     // iterMax of this pixel's view
-  uint32_t scnt;    // cnt at that saved step
+  uint32_t scnt;    // cnt at the start of the block
   bool live;        // still iterating (no escape seen, budget not spent)
-  bool pend;        // a saved step awaits resolve()
+  bool pend;        // a step of this block was not decided exactly: resolve() replays the block
 };
+
+// Start a pixel: the first step from z = 0 never escapes (R2 > 0) and leaves
+// z = c (with -0 read as +0), so it is taken here.
+__device__ __forceinline__ void lane_start(Lane& L, double cr, double ci, uint32_t lim) {
+  L.cr = cr;
+  L.ci = ci;
+  L.lim = lim;
+  L.cnt = lim ? 1u : 0u;
+  L.live = lim != 0u;
+  L.zr = plus_zero(cr);
+  L.zi = plus_zero(ci);
+  L.pend = false;
+}
+
+// Checkpoint at the start of a block of steps.
+__device__ __forceinline__ void block_begin(Lane& L) {
+  L.szr = L.zr;
+  L.szi = L.zi;
+  L.scnt = L.cnt;
+}
 
 // One step for one lane; straight-line code.  FILT selects the FP32 escape
 // filter (R2 in [2^-100, 2^100]); otherwise the test is the literal binary64
-// add and compare.
-template <bool FILT>
+// add and compare.  EMUL selects the integer-pipe products (else three FP64
+// multiplies, 2*zr by twice()).
+template <bool FILT, bool EMUL>
 __device__ __forceinline__ void step(Lane& L, double r2, EscThr thr) {
-  double zr2 = __dmul_rn(L.zr, L.zr);
-  double zi2 = __dmul_rn(L.zi, L.zi);
-  double t = __dmul_rn(twice(L.zr), L.zi);
+  double zr2, zi2, t;
+  bool odd = false;
+  if (EMUL) {
+    odd = !(emul_ok(L.zr) && emul_ok(L.zi));
+    zr2 = emul_sqr(L.zr);
+    zi2 = emul_sqr(L.zi);
+    t = emul_mul(L.zr, L.zi, 1);
+  } else {
+    zr2 = __dmul_rn(L.zr, L.zr);
+    zi2 = __dmul_rn(L.zi, L.zi);
+    t = __dmul_rn(twice(L.zr), L.zi);
+  }
   bool esc;
   if (FILT) {
     bool amb;
     esc = filter_sure(zr2, zi2, thr, amb);
-    bool first = amb && L.live && !L.pend;
-    L.szr = first ? L.zr : L.szr;
-    L.szi = first ? L.zi : L.szi;
-    L.scnt = first ? L.cnt : L.scnt;
-    L.pend = L.pend || first;
+    odd = odd || amb;
   } else {
     esc = __dadd_rn(zr2, zi2) > r2;
   }
+  L.pend = L.pend || (odd && L.live);
   bool upd = L.live && !esc && (L.cnt < L.lim);
   L.live = upd;
   L.cnt += upd ? 1u : 0u;
@@ -136,28 +217,39 @@ __device__ __forceinline__ void step(Lane& L, double r2, EscThr thr) {
   L.zr = __dadd_rn(__dsub_rn(zr2, zi2), L.cr);
 }
 
-// Settle a lane whose provisional run passed an undecided escape test: replay
-// from the saved step with the literal binary64 test up to the provisional
-// count; if an escape shows up earlier, that is the count.  Call
-// warp-uniformly between blocks of step() calls.
+// Settle a pending lane: redo the whole block from its checkpoint with the
+// literal binary64 operations -- STEPS exact steps, stopping at an escape or at
+// the budget -- and take that state and count.  Every block therefore moves a
+// lane STEPS steps forward or finishes it, whatever the provisional run did
+// (a lane whose every step is undecided, e.g. zi = 0 on the real axis, still
+// advances one exact block per block).  Call warp-uniformly between blocks.
+template <int STEPS>
 __device__ __forceinline__ void resolve(Lane& L, double r2) {
   if (__any_sync(FULL_MASK, L.pend)) {
     if (L.pend) {
       double zr = L.szr, zi = L.szi;
       uint32_t c = L.scnt;
-      while (c < L.cnt) {
+      bool live = true;
+      for (int k = 0; k < STEPS; ++k) {
+        if (c >= L.lim) {
+          live = false;
+          break;
+        }
         double zr2 = dmul_branch(zr, zr);
         double zi2 = dmul_branch(zi, zi);
-        if (dadd_branch(zr2, zi2) > r2) break;
+        if (dadd_branch(zr2, zi2) > r2) {
+          live = false;
+          break;
+        }
         double t = dmul_branch(twice(zr), zi);
         zi = dadd_branch(t, L.ci);
         zr = dadd_branch(dsub_branch(zr2, zi2), L.cr);
         ++c;
       }
-      if (c < L.cnt) {
-        L.cnt = c;
-        L.live = false;
-      }
+      L.cnt = c;
+      L.live = live;
+      L.zr = zr;
+      L.zi = zi;
       L.pend = false;
     }
   }

@@ -28,6 +28,7 @@ EscThr make_thr(double r2);
 int check_view(const mb_window* w, uint32_t m, uint32_t n, double r2, const void* out);
 int check_opts(const mb_opts* o, uint32_t* log2_tile);
 RenderFn render_fn(int kind, int sched, bool filt, int unroll);
+RenderFn render_fn_fp64(bool filt);
 int launch_render(const RenderFn fn, const RenderParams& P, uint32_t grid, uint32_t block, cudaStream_t st);
 // launch_render with the caller's optional timing events around it (opts->ev_start / ev_stop)
 int launch_render_timed(const RenderFn fn, const RenderParams& P, uint32_t grid, uint32_t block, cudaStream_t st,
@@ -37,5 +38,6 @@ int sm_count();
 int resident_ctas(const void* fn, int block);
 
 inline int opt_unroll(const mb_opts* o) { return o && o->unroll ? (int)o->unroll : (int)DEFAULT_UNROLL; }
+inline uint64_t opt_deadline_ns(const mb_opts* o) { return o && o->max_seconds ? o->max_seconds * 1000000000ull : 0ull; }
 
 }  // namespace mb

@@ -608,6 +608,7 @@ extern "C" int mb_probe(const mb_window* w, uint32_t m, uint32_t n, uint32_t ite
   P.status = opt ? opt->status : nullptr;
   P.probe_out = probe_out;
   P.n_items = V.tiles_x * V.tiles_y;
+  P.deadline_ns = opt_deadline_ns(opt);
   RenderFn fn = render_fn(KIND_PROBE, S_FCFS, filter_ok(escape_r2), opt_unroll(opt));
   uint32_t grid = opt && opt->grid ? opt->grid : default_grid(fn, block);
   uint32_t map_blocks = min((m + n + 255) / 256, 1024u);
@@ -652,6 +653,7 @@ extern "C" int mb_render_learned(const mb_window* w, uint32_t m, uint32_t n, uin
   P.log2_tile = log2_tile;
   P.counter = (uint32_t*)(ws + lay.counter);
   P.status = opt ? opt->status : nullptr;
+  P.deadline_ns = opt_deadline_ns(opt);
   // 1. pixel map + probe (writes its samples into the image too)
   uint32_t map_blocks = min((m + n + 255) / 256, 1024u);
   pixel_map_single_kernel<<<map_blocks, 256, 0, st>>>(V, (ViewDesc*)(ws + lay.view), P.counter);

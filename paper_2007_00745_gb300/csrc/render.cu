@@ -68,9 +68,9 @@ int check_opts(const mb_opts* o, uint32_t* log2_tile) {
 template <int KIND, int SCHED, bool FILT>
 static RenderFn pick_unroll(int unroll) {
   switch (unroll) {
-    case 4: return render_kernel<KIND, SCHED, FILT, 4>;
-    case 16: return render_kernel<KIND, SCHED, FILT, 16>;
-    default: return render_kernel<KIND, SCHED, FILT, 8>;
+    case 4: return render_kernel<KIND, SCHED, FILT, 4, true>;
+    case 16: return render_kernel<KIND, SCHED, FILT, 16, true>;
+    default: return render_kernel<KIND, SCHED, FILT, 8, true>;
   }
 }
 
@@ -89,6 +89,12 @@ RenderFn render_fn(int kind, int sched, bool filt, int unroll) {
   if (kind == KIND_PROBE) return pick_filt<KIND_PROBE, S_FCFS>(filt, unroll);
   if (kind == KIND_LIST) return pick_filt<KIND_LIST, S_FCFS>(filt, unroll);
   return pick_filt<KIND_BATCH, S_FCFS>(filt, unroll);
+}
+
+// All-FP64 products (three multiplies on the FP64 pipe): raster tiles only,
+// kept as the measured baseline of the integer-pipe products.
+RenderFn render_fn_fp64(bool filt) {
+  return filt ? render_kernel<KIND_RASTER, S_FCFS, true, 8, false> : render_kernel<KIND_RASTER, S_FCFS, false, 8, false>;
 }
 
 static std::mutex g_occ_mu;
@@ -214,6 +220,7 @@ extern "C" int mb_render(const mb_window* w, uint32_t m, uint32_t n, uint32_t it
   P.status = opt ? opt->status : nullptr;
   P.trace = opt ? opt->trace : nullptr;
   P.trace_len = opt && opt->trace ? opt->trace_len : 0;
+  P.deadline_ns = opt_deadline_ns(opt);
 
   int kind, s;
   switch (sched) {
@@ -224,6 +231,13 @@ extern "C" int mb_render(const mb_window* w, uint32_t m, uint32_t n, uint32_t it
     default: kind = KIND_RASTER; s = S_FCFS; P.n_items = tiles_x * tiles_y; break;
   }
   RenderFn fn = render_fn(kind, s, filter_ok(escape_r2), opt_unroll(opt));
+  if (opt && opt->fp64_products) {
+    if (kind != KIND_RASTER) {
+      if (owned) cudaFreeAsync(ws, st);
+      return MB_EINVAL;
+    }
+    fn = render_fn_fp64(filter_ok(escape_r2));
+  }
   uint32_t grid = opt && opt->grid ? opt->grid : default_grid(fn, block);
 
   uint32_t map_blocks = (m + n + 255) / 256;

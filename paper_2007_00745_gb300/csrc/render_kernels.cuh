@@ -45,6 +45,7 @@ struct BatchItem {
 // status bits
 constexpr uint32_t ST_SPIN_TIMEOUT = 1u;
 constexpr uint32_t ST_BAD_ITEM = 2u;
+constexpr uint32_t ST_DEADLINE = 4u;
 
 constexpr uint32_t END_ITEM = 0xFFFFFFFFu;
 constexpr int SPIN_LIMIT = 1 << 22;  // ~0.3 s at 64 ns per try: far above any real wait
@@ -62,6 +63,7 @@ struct RenderParams {
   uint32_t* status;            // error bits (may be null)
   mb_cta_trace* trace;         // per-CTA record (may be null)
   uint32_t trace_len;          // records available at `trace`
+  uint64_t deadline_ns;        // 0 = none; else a CTA stops (status ST_DEADLINE) once it has run this long
 };
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
@@ -208,14 +210,16 @@ __device__ __forceinline__ bool decode(const RenderParams& P, uint32_t it, uint3
   return ty < V.tiles_y && row < V.m && col < V.n;
 }
 
-template <int KIND, int SCHED, bool FILT, int UNROLL>
+template <int KIND, int SCHED, bool FILT, int UNROLL, bool EMUL>
 __global__ void __launch_bounds__(512) render_kernel(RenderParams P) {
   __shared__ unsigned long long s_word;
   __shared__ uint32_t s_taken;
+  __shared__ uint64_t s_t0;
   const int lane = threadIdx.x & 31;
   uint64_t t_start = 0;
   if (threadIdx.x == 0) {
     t_start = globaltimer_ns();
+    s_t0 = t_start;
     uint32_t it = first_item<SCHED>(P);
     s_word = (unsigned long long)it << 32;
     s_taken = it != END_ITEM ? 1u : 0u;
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(512) render_kernel(RenderParams P) {
 
   for (;;) {
     // Settle provisional escape decisions, then retire finished pixels.
-    resolve(L, r2);
+    resolve<UNROLL>(L, r2);
     if (has && !L.live) {
       *optr = L.cnt;
       if (KIND == KIND_PROBE && pptr) *pptr = L.cnt;
@@ -261,14 +265,7 @@ __global__ void __launch_bounds__(512) render_kernel(RenderParams P) {
         uint32_t v, row, col, tile;
         if (decode<KIND>(P, item, off + rank, v, row, col, tile)) {
           const ViewDesc& V = P.views[v];
-          L.cr = V.cx[col];
-          L.ci = V.cy[row];
-          L.zr = 0.0;
-          L.zi = 0.0;
-          L.cnt = 0;
-          L.lim = V.iter_max;
-          L.live = true;
-          L.pend = false;
+          lane_start(L, V.cx[col], V.cy[row], V.iter_max);
           r2 = V.r2;
           thr = V.thr;
           optr = V.out ? V.out + (size_t)row * V.n + col : nullptr;
@@ -285,8 +282,13 @@ __global__ void __launch_bounds__(512) render_kernel(RenderParams P) {
       idle = __ballot_sync(FULL_MASK, !has);
     }
     if (__ballot_sync(FULL_MASK, has) == 0) break;
+    if (P.deadline_ns && globaltimer_ns() - s_t0 > P.deadline_ns) {  // guard against a run-away launch
+      if (lane == 0) set_status(P, ST_DEADLINE);
+      break;
+    }
+    block_begin(L);
 #pragma unroll
-    for (int u = 0; u < UNROLL; ++u) step<FILT>(L, r2, thr);
+    for (int u = 0; u < UNROLL; ++u) step<FILT, EMUL>(L, r2, thr);
   }
 
   __syncthreads();

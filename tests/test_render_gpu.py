@@ -267,3 +267,23 @@ def test_escape_band_replay(orc, r2):
     got = gpu_render(win2, m2, n2, 100, r2=r2, sched="fcfs_tiles", tile=8)["img"]
     assert np.array_equal(got, want)
     assert want[1, 1] == orc.escape(0.5, 0.0, 100, r2)
+
+
+@pytest.mark.parametrize("r2", [4.0, 1e200])
+def test_fp64_products_baseline_matches(orc, r2):
+    """The all-FP64 products variant (the measured baseline) gives the same counts."""
+    win, m, n, it = (-1.9, 0.6, -1.2, 1.2), 150, 190, 1500
+    want = orc.render(win, m, n, it, r2)
+    a = gpu_render(win, m, n, it, r2=r2, sched="fcfs_tiles", tile=32, fp64_products=1)["img"]
+    b = gpu_render(win, m, n, it, r2=r2, sched="fcfs_tiles", tile=32)["img"]
+    assert np.array_equal(a, want) and np.array_equal(b, want)
+
+
+def test_real_axis_and_zero_column_replays(orc):
+    """Rows with c_im = 0 (zi stays 0: every step goes through the replay) and a
+    column with c_re = 0, with long interior orbits."""
+    win, m, n, it = (-2.0, 0.5, -1.0, 1.0), 64, 80, 5000   # row 32: c_im = 0; column 64: c_re = 0
+    want = orc.render(win, m, n, it)
+    for unroll in (4, 16):
+        got = gpu_render(win, m, n, it, sched="fcfs_tiles", tile=16, unroll=unroll)["img"]
+        assert np.array_equal(got, want)
