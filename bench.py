@@ -31,10 +31,11 @@ sys.path.insert(0, ROOT)
 
 ALG_OPS_PER_ITER = 8  # binary64 operations per escape step: 3 mul, 1 doubling, 4 add/sub
 
-# DRAM traffic of the render kernel from the ncu capture summarised in
-# profiles/, per rendered pixel; used only while the kernel sources still hash
-# to src_sha1 (otherwise the roofline reports traffic: null).
-NCU_RENDER = {"src_sha1": None, "dram_bytes_per_pixel": None}
+# DRAM traffic of the main render kernel from the ncu capture summarised in
+# profiles/render_kernel_list_8192x8192_it1000.md (dram read + write per launch
+# / pixels; traffic does not depend on iterMax, so it scales by pixel count);
+# used only while the kernel sources still hash to src_sha1, else null.
+NCU_RENDER = {"src_sha1": "13fed47939bee7c6748e020e666f7c69cf6c4247", "dram_bytes_per_pixel": 3.41}
 KERNEL_SOURCES = ("escape_core.cuh", "render_kernels.cuh")
 
 
