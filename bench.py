@@ -399,16 +399,17 @@ def run_ours(args):
         cmp = {}
         variants = [("naive", dict(sched="naive", tile=64)), ("alternating", dict(sched="alternating", tile=64)),
                     ("fcfs_rows", dict(sched="fcfs_rows", tile=64)), ("fcfs_tiles64", dict(sched="fcfs_tiles", tile=64)),
-                    ("fcfs_tiles16", dict(sched="fcfs_tiles", tile=16)), ("learned", None)]
+                    ("fcfs_tiles16", dict(sched="fcfs_tiles", tile=16)), ("learned", None), ("probe_sum", "probe")]
         for name, kw in variants:
             if kw is None and params is None:
                 continue
             tr = torch.zeros(g * 3, dtype=torch.int64, device=dev)
             a, b = E(), E()
             a.record(stream)
-            if kw is None:
-                mb.mb_render_learned(v.window, v.m, v.n, v.iter_max, v.r2, out, params, tile=args.tile,
-                                     block=args.block, unroll=args.unroll, grid=g, trace=tr, stream=stream)
+            if kw is None or kw == "probe":   # learned order, or its ablation ordered by the probe sum
+                mb.mb_render_learned(v.window, v.m, v.n, v.iter_max, v.r2, out, params if kw is None else None,
+                                     tile=args.tile, block=args.block, unroll=args.unroll, grid=g, trace=tr,
+                                     stream=stream)
             else:
                 mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, out, block=args.block, unroll=args.unroll,
                              grid=g, trace=tr, stream=stream, **kw)
@@ -465,6 +466,8 @@ def run_ours(args):
         zo = torch.empty(z.m * z.n, dtype=torch.int32, device=dev)
         runs = [("learned64", lambda: mb.mb_render_learned(z.window, z.m, z.n, z.iter_max, z.r2, zo, params, tile=64,
                                                           block=args.block, unroll=args.unroll)),
+                ("probe_sum64", lambda: mb.mb_render_learned(z.window, z.m, z.n, z.iter_max, z.r2, zo, None, tile=64,
+                                                            block=args.block, unroll=args.unroll)),
                 ("fcfs_tiles64", lambda: mb.mb_render(z.window, z.m, z.n, z.iter_max, z.r2, zo, sched="fcfs_tiles",
                                                      tile=64, block=args.block)),
                 ("fcfs_tiles16", lambda: mb.mb_render(z.window, z.m, z.n, z.iter_max, z.r2, zo, sched="fcfs_tiles",

@@ -307,7 +307,9 @@ int mb_order_split(const float* cost_pred, uint32_t ntiles, uint32_t tile, uint3
 /* The learned pipeline for one view: probe (its samples go straight into
  * `out`), features, network, order and split, then the FCFS render of the other
  * pixels over that list.  Same counts as mb_render.  opts->tile >= 16 (default
- * 64); opts->sched is ignored; opts->trace records the final render's CTAs. */
+ * 64); opts->sched is ignored; opts->trace records the final render's CTAs.
+ * params == NULL is the ablation without the network: each tile's cost is
+ * taken as log2(1 + (T*T/64) * sum of its probe counts) / 32. */
 int mb_render_learned(const mb_window* w, uint32_t m, uint32_t n, uint32_t iter_max, double escape_r2,
                       uint32_t* out, const float* params, const mb_opts* opt);
 

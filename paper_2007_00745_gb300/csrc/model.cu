@@ -61,6 +61,18 @@ __global__ void tile_targets_kernel(const unsigned long long* __restrict__ total
   if (t < ntiles) y[t] = (float)(log2(1.0 + (double)totals[t]) / 32.0);
 }
 
+// ablation without the network: a tile's cost predicted from its probe alone,
+// y = log2(1 + 64 * sum of the 64 probe counts) / 32 (the probe's estimate of the tile total)
+__global__ void probe_sum_cost_kernel(const uint32_t* __restrict__ probe, uint32_t ntiles, uint32_t tile,
+                                      float* __restrict__ y) {
+  uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  unsigned long long s = 0;
+  for (int k = 0; k < 64; ++k) s += probe[(size_t)t * 64 + k];
+  double scale = (double)tile * tile / 64.0;
+  y[t] = (float)(log2(1.0 + scale * (double)s) / 32.0);
+}
+
 // ---- MLP forward --------------------------------------------------------------
 
 constexpr int FWD_S = 16;  // samples per pass of a forward block (64 threads, one per hidden unit)
@@ -623,7 +635,6 @@ extern "C" int mb_render_learned(const mb_window* w, uint32_t m, uint32_t n, uin
                                  uint32_t* out, const float* params, const mb_opts* opt) {
   int rc = check_view(w, m, n, escape_r2, out);
   if (rc) return rc;
-  if (!params) return MB_EINVAL;
   uint32_t log2_tile = 0;
   rc = check_opts(opt, &log2_tile);
   if (rc) return rc;
@@ -663,8 +674,13 @@ extern "C" int mb_render_learned(const mb_window* w, uint32_t m, uint32_t n, uin
   rc = cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
   if (rc == MB_OK) rc = launch_render(fprobe, PP, default_grid(fprobe, block), block, st);
   // 2. features, 3. predicted cost, 4. longest-first items with splits
-  if (rc == MB_OK) rc = mb_tile_features(PP.probe_out, w, m, n, iter_max, tile, (float*)(ws + lay.feat), st);
-  if (rc == MB_OK) rc = mb_mlp_forward(params, (const float*)(ws + lay.feat), nt, (float*)(ws + lay.y), st);
+  if (params) {
+    if (rc == MB_OK) rc = mb_tile_features(PP.probe_out, w, m, n, iter_max, tile, (float*)(ws + lay.feat), st);
+    if (rc == MB_OK) rc = mb_mlp_forward(params, (const float*)(ws + lay.feat), nt, (float*)(ws + lay.y), st);
+  } else if (rc == MB_OK) {
+    probe_sum_cost_kernel<<<(nt + 255) / 256, 256, 0, st>>>(PP.probe_out, nt, tile, (float*)(ws + lay.y));
+    rc = cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
+  }
   if (rc == MB_OK) {
     order_split_kernel<<<1, OS_T, 0, st>>>((const float*)(ws + lay.y), nt, tile, grid, (uint8_t*)(ws + lay.qbuf),
                                            (uint32_t*)(ws + lay.order), (mb_item*)(ws + lay.items), cap,

@@ -76,16 +76,16 @@ class SplitMix64:
         return lo + self.next_u64() % (hi - lo + 1)
 
 
-def training_zoom_views(count, side, seed=SEED + 3, iter_max_range=(2048, 32768)):
-    """Seeded zoom windows for training the tile-cost model: centres drawn from
-    the boundary manifest, widths log-uniform in [1e-7, 1e-2].  Never config 3's
-    own window."""
+def training_zoom_views(count, side, seed=SEED + 3, iter_max_range=(2048, 32768), log10_width=(-7.0, 0.5)):
+    """Seeded windows for training the tile-cost model: centres drawn from the
+    boundary manifest, widths log-uniform in 10^log10_width (deep zooms up to
+    views of the whole set).  Never one of the benchmark's own windows."""
     man = boundary_points()
     rng = SplitMix64(seed)
     out = []
     for _ in range(count):
         cx, cy = man[rng.randint(0, len(man) - 1)]
-        width = 10.0 ** (-7.0 + 5.0 * rng.uniform())
+        width = 10.0 ** (log10_width[0] + (log10_width[1] - log10_width[0]) * rng.uniform())
         it = int(round(2.0 ** (math.log2(iter_max_range[0]) + rng.uniform()
                                * (math.log2(iter_max_range[1]) - math.log2(iter_max_range[0])))))
         out.append(View(zoom_window(cx, cy, width, side, side), side, side, it))

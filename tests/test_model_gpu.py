@@ -195,3 +195,11 @@ def test_save_load_roundtrip(small_model):
             f.write(b"XXXX")
         with pytest.raises(mb.MBError):
             mb.mb_model_load(path, q)
+
+
+def test_probe_sum_ablation_is_bit_exact(orc):
+    v = wl.View(wl.zoom_window(-0.74364, 0.13182, 3e-5, 257, 300), 257, 300, 4000)
+    out = torch.full((v.m * v.n,), -1, dtype=torch.int32, device="cuda")
+    mb.mb_render_learned(v.window, v.m, v.n, v.iter_max, v.r2, out, None, tile=32)
+    torch.cuda.synchronize()
+    assert np.array_equal(_u32(out).reshape(v.m, v.n), orc.render(v.window, v.m, v.n, v.iter_max, v.r2))
