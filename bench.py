@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--sched", default="learned",
                    help="learned (default) or a plain scheduler: naive, alternating, fcfs_rows, fcfs_tiles")
-    p.add_argument("--tile", type=int, default=64)
+    p.add_argument("--tile", type=int, default=32)
     p.add_argument("--block", type=int, default=512)
     p.add_argument("--unroll", type=int, default=8)
     p.add_argument("--no-cpu-baseline", action="store_true")

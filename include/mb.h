@@ -95,6 +95,7 @@ typedef struct {
                                 ran out, 2 = an item outside its tile, 4 = max_seconds reached) */
   void* workspace;           /* device, optional: temporary memory, >= mb_render_workspace_size() bytes, 256-byte aligned */
   size_t workspace_bytes;
+  uint32_t split;            /* mb_render_learned: split divisor S of the order-and-split rule; 0 = 4 */
   uint32_t max_seconds;      /* 0 = no limit; else each CTA of the main render stops after running this long
                                 and ORs 4 into *status (a guard for interactive use; the image is then incomplete) */
   uint32_t fp64_products;    /* 1 = form the three products of a step on the FP64 pipe (MB_SCHED_FCFS_TILES
@@ -245,17 +246,19 @@ int mb_serve_destroy(mb_server* s);
  * the last row / column.  Features (70 floats per tile, FP32):
  *   f[8a+b] = log2(1 + probe[a][b]) / log2(1 + iterMax); f[64] = (tx+0.5)/tiles_x;
  *   f[65] = (ty+0.5)/tiles_y; f[66] = log2(1 + iterMax)/17;
- *   f[67] = -log10((xmax - xmin)/n)/16; f[68] = mean(f[0..63]);
+ *   f[67] = -log10((xmax - xmin)/n)/16; f[68] = log2(1 + (T*T/64) * sum of the probe)/32;
  *   f[69] = (samples at iterMax)/64.
- * Network: 70 -> 64 -> 64 -> 1, ReLU, FP32; flat parameters (MB_MLP_PARAMS)
- *   W1[64][70], b1[64], W2[64][64], b2[64], W3[64], b3 (row-major W[out][in]).
+ * Network: 70 -> 64 -> 64 -> 1, ReLU, FP32, residual on the probe-sum feature:
+ *   y = f[68] + W3 . relu(W2 relu(W1 f + b1) + b2) + b3; flat parameters
+ *   (MB_MLP_PARAMS) W1[64][70], b1[64], W2[64][64], b2[64], W3[64], b3 (row-major W[out][in]).
  * Target: log2(1 + tile total)/32; loss: mean squared error over the batch.
  * Adam: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
  *   p -= lr (m/(1-b1^t)) / (sqrt(v/(1-b2^t)) + eps).
  * Order and split (integers after one FP32 rounding): q = 0 if y <= 0 else
  *   min(trunc(fp32(y*128)), 191); tiles sorted by q descending, ties by tile
  *   index; c(q) = (2^(q>>2) * {65536,77936,92682,110218}[q&3]) >> 16 (uint64);
- *   target = max(1, (saturating sum of c) / (4 G)), G = CTAs of the render;
+ *   target = max(1, (saturating sum of c) / (S G)), G = CTAs of the render,
+ *   S = the split divisor (default 4; larger S cuts heavy tiles into more strips);
  *   s = smallest power of two >= ceil(c/target), at most min(16, T/4); the
  *   tile yields items (tile, k*T/s, T/s), k < s, in sorted order. */
 #define MB_MLP_PARAMS 8769
@@ -297,12 +300,13 @@ int mb_adam_step(float* params, const float* grad, float* m, float* v, uint32_t 
 int mb_model_train(float* params, float* adam_m, float* adam_v, const float* x, const float* target, uint32_t count,
                    const uint32_t* order, uint32_t epochs, uint32_t batch, float lr, float* epoch_loss, void* stream);
 
-/* Work list from predicted tile costs (device, ntiles floats): items (device,
+/* Work list from predicted tile costs (device, ntiles floats), split divisor
+ * S = split (0 = 4, at most 4096): items (device,
  * capacity entries) and their number (device uint32), per the rule above.
  * capacity >= 16 * ntiles always suffices; if it is exceeded, *n_items = 0 and
  * bit 2 is ORed into *status (device, may be NULL). */
-int mb_order_split(const float* cost_pred, uint32_t ntiles, uint32_t tile, uint32_t grid, mb_item* items,
-                   uint32_t capacity, uint32_t* n_items, uint32_t* status, void* stream);
+int mb_order_split(const float* cost_pred, uint32_t ntiles, uint32_t tile, uint32_t grid, uint32_t split,
+                   mb_item* items, uint32_t capacity, uint32_t* n_items, uint32_t* status, void* stream);
 
 /* The learned pipeline for one view: probe (its samples go straight into
  * `out`), features, network, order and split, then the FCFS render of the other

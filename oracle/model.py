@@ -14,12 +14,13 @@ iteration budget I), from its probe counts p[a][b] (the oracle's mbo_probe):
     f[65]   = (ty + 0.5) / tiles_y
     f[66]   = log2(1 + I) / 17
     f[67]   = -log10((xmax - xmin) / n) / 16
-    f[68]   = mean(f[0:64])
+    f[68]   = log2(1 + (T*T/64) * sum_ab p[a][b]) / 32   (the probe's estimate of the tile total)
     f[69]   = (number of p == I) / 64
 
 network (row-major W[out][in], flat parameter vector in this order):
     W1[64][70], b1[64], W2[64][64], b2[64], W3[64], b3
-    h1 = relu(W1 x + b1); h2 = relu(W2 h1 + b2); y = W3 . h2 + b3
+    h1 = relu(W1 x + b1); h2 = relu(W2 h1 + b2); y = x[68] + W3 . h2 + b3
+    (a residual on the probe-sum estimate f[68]: the network learns corrections)
 target:  y* = log2(1 + tile total) / 32;  loss = mean over the batch of (y - y*)^2
 Adam (Kingma & Ba 2015):  m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
     p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)
@@ -28,7 +29,8 @@ order and split (integers after one FP32 quantisation):
     q_t = 0 if y_t <= 0 else min(int(float32(y_t) * float32(128)), 191)
     tiles sorted by q descending, ties by tile index ascending (stable)
     c(q) = (2^(q >> 2) * M[q & 3]) >> 16,  M = [65536, 77936, 92682, 110218]
-    target = max(1, (sum_t c(q_t)) // (4 G))        G = number of CTAs; the sum
+    target = max(1, (sum_t c(q_t)) // (S G))        G = number of CTAs, S the split
+                                                     divisor (default 4); the sum
                                                      saturates at 2^64 - 1
     s_t = smallest power of two >= ceil(c(q_t) / target), at most min(16, T / 4)
     items: for each tile in sorted order, rows [k T/s_t, (k+1) T/s_t), k < s_t
@@ -72,7 +74,7 @@ def features(probe, window, m, n, iter_max, tile):
     f[:, 65] = (t // tiles_x + 0.5) / tiles_y
     f[:, 66] = denom / 17.0
     f[:, 67] = -np.log10((window[1] - window[0]) / n) / 16.0
-    f[:, 68] = f[:, :64].mean(axis=1)
+    f[:, 68] = np.log2(1.0 + (tile * tile / 64.0) * probe.sum(axis=1)) / 32.0
     f[:, 69] = (probe == iter_max).sum(axis=1) / 64.0
     return f
 
@@ -83,7 +85,7 @@ def forward(params, X):
     X = np.asarray(X, dtype=np.float64)
     h1 = np.maximum(X @ W1.T + b1, 0.0)
     h2 = np.maximum(h1 @ W2.T + b2, 0.0)
-    y = h2 @ W3 + b3
+    y = X[:, 68] + h2 @ W3 + b3
     return y, h1, h2
 
 
@@ -134,13 +136,13 @@ def level_cost(q):
                     dtype=np.uint64)
 
 
-def order_and_split(y, tile, grid):
+def order_and_split(y, tile, grid, split=4):
     """Item list [(tile, row0, rows)] for predicted costs y (one per tile)."""
     q = cost_level(y)
     order = np.argsort(-q, kind="stable")
     c = [int(x) for x in level_cost(q)]
     total = min(sum(c), 2 ** 64 - 1)
-    target = max(1, total // (4 * grid))
+    target = max(1, total // (split * grid))
     smax = min(16, tile // 4)
     items = []
     for t in order:

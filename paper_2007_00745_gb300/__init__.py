@@ -49,7 +49,7 @@ def _stream(stream):
 
 def _opts(sched="fcfs_tiles", tile=0, grid=0, block=0, unroll=0, stream=None, items=None, n_items=0,
           tile_totals=None, trace=None, trace_len=0, status=None, workspace=None, workspace_bytes=0,
-          events=None, fp64_products=0, max_seconds=300):
+          events=None, fp64_products=0, max_seconds=300, split=0):
     L = _L()
     o = L.mb_opts()
     o.sched = SCHEDS[sched] if isinstance(sched, str) else int(sched)
@@ -64,6 +64,7 @@ def _opts(sched="fcfs_tiles", tile=0, grid=0, block=0, unroll=0, stream=None, it
     o.status = _ptr(status)
     o.fp64_products = int(fp64_products)
     o.max_seconds = int(max_seconds)
+    o.split = int(split)
     if events is not None:   # (start, stop) torch.cuda.Event pair recorded around the main render kernel
         handles = []
         for ev in events:
@@ -206,8 +207,8 @@ def mb_model_train(params, adam_m, adam_v, x, target, count, order, epochs, batc
                                      _stream(stream)), "mb_model_train")
 
 
-def mb_order_split(cost_pred, ntiles, tile, grid, items, capacity, n_items, status=None, stream=None):
-    _check(_L().lib().mb_order_split(_ptr(cost_pred), int(ntiles), int(tile), int(grid), _ptr(items),
+def mb_order_split(cost_pred, ntiles, tile, grid, items, capacity, n_items, status=None, stream=None, split=4):
+    _check(_L().lib().mb_order_split(_ptr(cost_pred), int(ntiles), int(tile), int(grid), int(split), _ptr(items),
                                      int(capacity), _ptr(n_items), _ptr(status), _stream(stream)), "mb_order_split")
 
 

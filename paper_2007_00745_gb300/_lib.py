@@ -32,7 +32,7 @@ class mb_cta_trace(ctypes.Structure):
 class mb_opts(ctypes.Structure):
     _fields_ = [("sched", i32), ("tile", u32), ("grid", u32), ("block", u32), ("unroll", u32),
                 ("stream", vp), ("items", vp), ("n_items", u32), ("tile_totals", vp), ("trace", vp), ("trace_len", u32),
-                ("status", vp), ("workspace", vp), ("workspace_bytes", sz), ("max_seconds", u32), ("fp64_products", u32),
+                ("status", vp), ("workspace", vp), ("workspace_bytes", sz), ("split", u32), ("max_seconds", u32), ("fp64_products", u32),
                 ("ev_start", vp), ("ev_stop", vp)]
 
 
@@ -90,7 +90,7 @@ def _load():
     L.mb_adam_step.argtypes = [vp, vp, vp, vp, u32, u32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                ctypes.c_float, vp]
     L.mb_model_train.argtypes = [vp, vp, vp, vp, vp, u32, vp, u32, u32, ctypes.c_float, vp, vp]
-    L.mb_order_split.argtypes = [vp, u32, u32, u32, vp, u32, vp, vp, vp]
+    L.mb_order_split.argtypes = [vp, u32, u32, u32, u32, vp, u32, vp, vp, vp]
     L.mb_render_learned.argtypes = [P(mb_window), u32, u32, u32, f64, vp, vp, P(mb_opts)]
     L.mb_model_save.argtypes = [vp, ctypes.c_char_p]
     L.mb_model_load.argtypes = [ctypes.c_char_p, vp]

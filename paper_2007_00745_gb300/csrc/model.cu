@@ -30,20 +30,19 @@ static_assert(P_COUNT == MB_MLP_PARAMS, "parameter count");
 
 __global__ void features_kernel(const uint32_t* __restrict__ probe, uint32_t ntiles, uint32_t tiles_x,
                                 uint32_t tiles_y, uint32_t iter_max, double xmin, double xmax, uint32_t n,
-                                float* __restrict__ feat) {
+                                uint32_t tile, float* __restrict__ feat) {
   uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ntiles) return;
   const double log_i = log2(1.0 + (double)iter_max);
   const float inv = (float)(1.0 / log_i);
   const uint32_t* p = probe + (size_t)t * 64;
   float* f = feat + (size_t)t * NF;
-  float sum = 0.0f;
+  unsigned long long sum = 0;
   uint32_t full = 0;
   for (int k = 0; k < 64; ++k) {
     uint32_t c = p[k];
-    float v = __fmul_rn(log2f(1.0f + (float)c), inv);
-    f[k] = v;
-    sum = __fadd_rn(sum, v);
+    f[k] = __fmul_rn(log2f(1.0f + (float)c), inv);
+    sum += c;
     full += c == iter_max ? 1u : 0u;
   }
   uint32_t tx = t % tiles_x, ty = t / tiles_x;
@@ -51,7 +50,7 @@ __global__ void features_kernel(const uint32_t* __restrict__ probe, uint32_t nti
   f[65] = (float)((ty + 0.5) / tiles_y);
   f[66] = (float)(log_i / 17.0);
   f[67] = (float)(-log10((xmax - xmin) / (double)n) / 16.0);
-  f[68] = sum / 64.0f;
+  f[68] = (float)(log2(1.0 + (double)tile * tile / 64.0 * (double)sum) / 32.0);
   f[69] = (float)full / 64.0f;
 }
 
@@ -116,7 +115,7 @@ __global__ void __launch_bounds__(64) mlp_forward_kernel(const float* __restrict
       if ((j & 31) == 0) red[j >> 5][s] = part;
     }
     __syncthreads();
-    if (j < FWD_S && base + j < N) y[base + j] = b3 + red[0][j] + red[1][j];
+    if (j < FWD_S && base + j < N) y[base + j] = xs[j][68] + b3 + red[0][j] + red[1][j];
     __syncthreads();
   }
 }
@@ -286,7 +285,7 @@ __device__ __forceinline__ unsigned long long sat_add(unsigned long long a, unsi
 }
 
 __global__ void __launch_bounds__(OS_T) order_split_kernel(const float* __restrict__ y, uint32_t ntiles, uint32_t tile,
-                                                           uint32_t grid, uint8_t* __restrict__ qbuf,
+                                                           uint32_t grid, uint32_t split, uint8_t* __restrict__ qbuf,
                                                            uint32_t* __restrict__ order, mb_item* __restrict__ items,
                                                            uint32_t capacity, uint32_t* __restrict__ n_items,
                                                            uint32_t* __restrict__ status) {
@@ -345,7 +344,7 @@ __global__ void __launch_bounds__(OS_T) order_split_kernel(const float* __restri
     __syncthreads();
   }
   // strips per tile in sorted order, exclusive scan, items
-  unsigned long long target = csum[0] / (4ull * grid);
+  unsigned long long target = csum[0] / ((unsigned long long)split * grid);
   if (target < 1) target = 1;
   uint32_t smax = tile / 4 < 16 ? tile / 4 : 16;
   uint32_t per = (ntiles + OS_T - 1) / OS_T;
@@ -403,7 +402,7 @@ extern "C" int mb_tile_features(const uint32_t* probe, const mb_window* w, uint3
   if (!probe || !w || !feat || m == 0 || n == 0 || tile < 16 || tile > 256 || (tile & (tile - 1))) return MB_EINVAL;
   uint32_t tx = (n + tile - 1) / tile, ty = (m + tile - 1) / tile, nt = tx * ty;
   features_kernel<<<(nt + 127) / 128, 128, 0, (cudaStream_t)stream>>>(probe, nt, tx, ty, iter_max, w->xmin, w->xmax, n,
-                                                                       feat);
+                                                                       tile, feat);
   return cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
 }
 
@@ -500,11 +499,12 @@ extern "C" int mb_model_train(float* params, float* adam_m, float* adam_v, const
   return rc;
 }
 
-extern "C" int mb_order_split(const float* cost_pred, uint32_t ntiles, uint32_t tile, uint32_t grid, mb_item* items,
-                              uint32_t capacity, uint32_t* n_items, uint32_t* status, void* stream) {
+extern "C" int mb_order_split(const float* cost_pred, uint32_t ntiles, uint32_t tile, uint32_t grid, uint32_t split,
+                              mb_item* items, uint32_t capacity, uint32_t* n_items, uint32_t* status, void* stream) {
   if (!cost_pred || !items || !n_items || ntiles == 0 || grid == 0 || tile < 8 || tile > 256 ||
-      (tile & (tile - 1)))
+      (tile & (tile - 1)) || split > 4096)
     return MB_EINVAL;
+  if (split == 0) split = 4;
   cudaStream_t st = (cudaStream_t)stream;
   size_t bytes = a256(ntiles) + a256((size_t)ntiles * 4);
   char* ws = nullptr;
@@ -512,7 +512,7 @@ extern "C" int mb_order_split(const float* cost_pred, uint32_t ntiles, uint32_t 
     cudaGetLastError();
     return MB_ENOMEM;
   }
-  order_split_kernel<<<1, OS_T, 0, st>>>(cost_pred, ntiles, tile, grid, (uint8_t*)ws, (uint32_t*)(ws + a256(ntiles)),
+  order_split_kernel<<<1, OS_T, 0, st>>>(cost_pred, ntiles, tile, grid, split, (uint8_t*)ws, (uint32_t*)(ws + a256(ntiles)),
                                          items, capacity, n_items, status);
   int rc = cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
   cudaFreeAsync(ws, st);
@@ -682,7 +682,9 @@ extern "C" int mb_render_learned(const mb_window* w, uint32_t m, uint32_t n, uin
     rc = cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
   }
   if (rc == MB_OK) {
-    order_split_kernel<<<1, OS_T, 0, st>>>((const float*)(ws + lay.y), nt, tile, grid, (uint8_t*)(ws + lay.qbuf),
+    uint32_t split = opt && opt->split ? opt->split : 4u;
+    if (split > 4096) split = 4096;
+    order_split_kernel<<<1, OS_T, 0, st>>>((const float*)(ws + lay.y), nt, tile, grid, split, (uint8_t*)(ws + lay.qbuf),
                                            (uint32_t*)(ws + lay.order), (mb_item*)(ws + lay.items), cap,
                                            (uint32_t*)(ws + lay.nitems), P.status);
     rc = cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;

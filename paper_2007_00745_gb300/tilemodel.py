@@ -59,7 +59,7 @@ def default_model(train_views=32, side=1024, tile=64, epochs=40, stream=None, ca
     (training_zoom_views), cached under _build/ keyed by its recipe."""
     import torch
     recipe = {"views": train_views, "side": side, "tile": tile, "epochs": epochs, "seed": wl.SEED,
-              "lib": mb.mb_version()}
+              "lib": mb.mb_version(), "features": "probe-sum-residual-v3"}
     key = hashlib.sha1(json.dumps(recipe, sort_keys=True).encode()).hexdigest()[:12]
     path = os.path.join(CACHE_DIR, "tile_model_%s.bin" % key)
     params = torch.empty(mb.MB_MLP_PARAMS, dtype=torch.float32, device="cuda")

@@ -152,13 +152,14 @@ def _normals(rng, count):
 
 def mlp_init(seed=SEED + 6):
     """Initial network parameters (float32, the C ABI's flat layout): He-normal
-    weights, zero hidden biases, output bias 0.5."""
+    hidden weights, zero biases, and a small output layer, so that the network
+    starts as its residual input (the probe-sum estimate) plus a small correction."""
     import numpy as np
     rng = SplitMix64(seed)
     w1 = np.array(_normals(rng, MLP_HID * MLP_IN)) * math.sqrt(2.0 / MLP_IN)
     w2 = np.array(_normals(rng, MLP_HID * MLP_HID)) * math.sqrt(2.0 / MLP_HID)
-    w3 = np.array(_normals(rng, MLP_HID)) * math.sqrt(1.0 / MLP_HID)
-    p = np.concatenate([w1, np.zeros(MLP_HID), w2, np.zeros(MLP_HID), w3, [0.5]])
+    w3 = np.array(_normals(rng, MLP_HID)) * (0.05 / math.sqrt(MLP_HID))
+    p = np.concatenate([w1, np.zeros(MLP_HID), w2, np.zeros(MLP_HID), w3, [0.0]])
     return p.astype(np.float32)
 
 

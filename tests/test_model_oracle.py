@@ -34,14 +34,15 @@ def test_gradient_matches_finite_differences():
 
 def test_linear_special_case_equals_matrix_product():
     # Non-negative inputs, weights and biases keep every ReLU in its linear part,
-    # so the network is the product W3 W2 W1 x plus the propagated biases.
+    # so the network is the product W3 W2 W1 x plus the propagated biases (plus x[68]).
     rng = np.random.default_rng(2)
     W1 = rng.uniform(0, 0.1, (64, 70)); b1 = rng.uniform(0, 0.1, 64)
     W2 = rng.uniform(0, 0.1, (64, 64)); b2 = rng.uniform(0, 0.1, 64)
     W3 = rng.uniform(0, 0.1, 64); b3 = 0.25
     X = rng.uniform(0, 1, (5, 70))
     y, _, _ = M.forward(M.pack(W1, b1, W2, b2, W3, b3), X)
-    want = np.linalg.multi_dot([W3, W2, W1, X.T]) + np.linalg.multi_dot([W3, W2, b1]) + W3 @ b2 + b3
+    want = (np.linalg.multi_dot([W3, W2, W1, X.T]) + np.linalg.multi_dot([W3, W2, b1]) + W3 @ b2 + b3
+            + X[:, 68])   # the residual input
     assert np.allclose(y, want, rtol=1e-12, atol=1e-12)
 
 
@@ -74,9 +75,11 @@ def test_features_hand_values():
     probe[1, :, :4] = 7
     f = M.features(probe, (-2.0, 2.0, -1.0, 1.0), 100, 64, 255, 64)
     assert f.shape == (2, 70)
-    assert np.allclose(f[0, :64], 1.0) and f[0, 69] == 1.0 and f[0, 68] == 1.0
+    assert np.allclose(f[0, :64], 1.0) and f[0, 69] == 1.0
     assert np.allclose(f[1, :4], 3.0 / 8.0) and np.allclose(f[1, 4:8], 0.0) and f[1, 69] == 0.0
-    assert f[1, 68] == pytest.approx(3.0 / 16.0)
+    # probe-sum estimate: tile 0 sums 64 * 255 -> 64 * 64 * 255 = 1044480; tile 1 sums 32 * 7 -> 64 * 224 = 14336
+    assert f[0, 68] == pytest.approx(np.log2(1.0 + 1044480.0) / 32.0)
+    assert f[1, 68] == pytest.approx(np.log2(1.0 + 14336.0) / 32.0)
     assert f[0, 64] == 0.5 and f[0, 65] == 0.25 and f[1, 65] == 0.75
     assert f[0, 66] == pytest.approx(8.0 / 17.0)
     assert f[0, 67] == pytest.approx(-np.log10(4.0 / 64.0) / 16.0)
@@ -94,6 +97,14 @@ def test_order_and_split_hand_example():
     items = M.order_and_split([0.25, 0.5, 0.25], 64, 2)
     assert items[:8] == [(1, 8 * k, 8) for k in range(8)]
     assert items[8:] == [(0, 0, 64), (2, 0, 64)]
+
+
+def test_split_divisor_hand_example():
+    # same three tiles, S = 16: target = 66048 // 32 = 2064; tile 1 (c = 65536) needs 32 strips,
+    # capped at min(16, 64/4) = 16 strips of 4 rows; tiles 0 and 2 (c = 256) stay whole.
+    items = M.order_and_split([0.25, 0.5, 0.25], 64, 2, split=16)
+    assert items[:16] == [(1, 4 * k, 4) for k in range(16)]
+    assert items[16:] == [(0, 0, 64), (2, 0, 64)]
 
 
 def test_order_and_split_invariants():
