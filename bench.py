@@ -57,8 +57,12 @@ def parse():
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--zoom", action="store_true", help="add the 16384^2 deep-zoom comparison (about a minute)")
+    p.add_argument("--table2", action="store_true",
+                   help="add the GPU analogue of the paper's Table II: speed-up over one worker (CTA) of the "
+                        "naive, alternating and FCFS row schemes on the paper's test shape (2000^2 sample)")
     p.add_argument("--serve-sweep", default="", help="comma-separated request rates for a serving sweep")
     p.add_argument("--serve-count", type=int, default=100)
+    p.add_argument("--ppm", default="", help="also write the headline image there (default: a temporary file)")
     p.add_argument("--size", type=int, default=0, help="override m = n (profiling runs)")
     p.add_argument("--iter-max", type=int, default=0, help="override iterMax (profiling runs)")
     p.add_argument("--cpu-rows-stride", type=int, default=2)
@@ -393,6 +397,26 @@ def run_ours(args):
                        "d2h_bytes_per_step": v.m * v.n * 4, "ms_per_step": ems,
                        "note": "inputs are five scalars passed by value; counts copied to pinned host memory"}
 
+    if not args.no_e2e:
+        # The paper's two timings (Sec. IV listing): computation, and total including the image file.
+        rgb = torch.empty(v.m * v.n * 3, dtype=torch.uint8, device=dev)
+        rgb_host = torch.empty(v.m * v.n * 3, dtype=torch.uint8, pin_memory=True)
+        path = args.ppm or os.path.join(tempfile.mkdtemp(prefix="mb_ppm_"), "Mandelbrot.ppm")
+        torch.cuda.synchronize()
+        t_a = time.perf_counter()
+        step()
+        torch.cuda.synchronize()
+        t_b = time.perf_counter()
+        mb.mb_colorize(out, v.iter_max, rgb, stream=stream)
+        rgb_host.copy_(rgb, non_blocking=True)
+        torch.cuda.synchronize()
+        mb.mb_write_ppm(path, rgb_host, v.m, v.n)
+        t_c = time.perf_counter()
+        line["paper_timings"] = {"computational_s": t_b - t_a, "total_s": t_c - t_a, "ppm_bytes": os.path.getsize(path)}
+        if not args.ppm:
+            os.unlink(path)
+            os.rmdir(os.path.dirname(path))
+
     if not args.no_compare:
         sms, per = mb.mb_device_info(args.block)
         g = sms * per
@@ -490,6 +514,34 @@ def run_ours(args):
         for k in zc:
             zc[k]["giter_s"] = zi / (zc[k]["ms"] * 1e-3) / 1e9
         line["zoom16384"] = {"iterations": zi, "variants": zc}
+
+    if args.table2:
+        from paper_2007_00745_gb300 import report
+        p = wl.PAPER_SHAPE
+        pv = wl.scaled(p, 2000, 2000)   # same window, budget and R^2 as Sec. IV's test, 1/16 of the pixels
+        po = torch.empty(pv.m * pv.n, dtype=torch.int32, device=dev)
+        workers = [1, 2, 4, 8, 16, 32, 64, 152, 304]
+        times = {}
+        for sched in ("naive", "alternating", "fcfs_rows"):
+            times[sched] = {}
+            for g in workers:
+                a, b = E(), E()
+                a.record()
+                mb.mb_render(pv.window, pv.m, pv.n, pv.iter_max, pv.r2, po, sched=sched, grid=g, block=args.block,
+                             unroll=args.unroll)
+                b.record()
+                b.synchronize()
+                times[sched][g] = a.elapsed_time(b) * 1e-3
+        mb.mb_sum_counts(po, total)
+        torch.cuda.synchronize()
+        tab = report.scaling_table(times)
+        line["table2"] = {"workload": "2000x2000 re[-2,1] im[-1.5,1.5] iterMax 2000 R2 160000 (paper Sec. IV shape, "
+                                      "1/16 of its pixels); workers = CTAs of %d threads" % args.block,
+                          "iterations": int(total.item()),
+                          "seconds": {s_: {str(g): t for g, t in r.items()} for s_, r in times.items()},
+                          "speedup": {s_: {str(g): round(x[0], 3) for g, x in r.items()} for s_, r in tab.items()},
+                          "pct_diff_vs_linear": {s_: {str(g): round(x[1], 2) for g, x in r.items()}
+                                                 for s_, r in tab.items()}}
 
     if not args.no_cpu_baseline:
         it, dt, nrows, cores = cpu_sample(v, args.cpu_rows_stride)

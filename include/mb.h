@@ -322,6 +322,17 @@ int mb_render_learned(const mb_window* w, uint32_t m, uint32_t n, uint32_t iter_
 int mb_model_save(const float* params, const char* path);
 int mb_model_load(const char* path, float* params);
 
+/* ---- output: iteration -> colour (Sec. I) and the image file (Sec. IV) ----
+ * Palette (the paper names none): k == iter_max -> black; otherwise
+ * r = tri(7k mod 512), g = tri(5k mod 512), b = tri(3k mod 512),
+ * tri(x) = x < 256 ? x : 511 - x.  rgb: 3 bytes per pixel, row-major. */
+
+/* Colours (device, 3*count bytes) of counts (device). */
+int mb_colorize(const uint32_t* counts, uint64_t count, uint32_t iter_max, uint8_t* rgb, void* stream);
+
+/* Writes a binary PPM (P6, maxval 255) of m rows x n columns from rgb (host). */
+int mb_write_ppm(const char* path, const uint8_t* rgb, uint32_t m, uint32_t n);
+
 /* FP64 issue-rate microbenchmark: runs independent chains of one binary64
  * operation (op: 0 = add, 1 = mul, 2 = fma) on every SM and returns the
  * measured rate in operations per second (a fused multiply-add counts as one

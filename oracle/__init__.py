@@ -41,6 +41,7 @@ def lib():
         L.mbo_alternating_owner.argtypes = [u32, u32]
         L.mbo_alternating_owner.restype = u32
         L.mbo_max_threads.restype = i32
+        L.mbo_colorize.argtypes = [p, u64, u32, p]
         _lib = L
     return _lib
 
@@ -128,3 +129,11 @@ def alternating_owner(i, workers):
 
 def max_threads():
     return int(lib().mbo_max_threads())
+
+
+def colorize(counts, iter_max):
+    """RGB bytes (count x 3) of the counts under the palette of mbo_colorize."""
+    counts = np.ascontiguousarray(counts, dtype=np.uint32).reshape(-1)
+    out = np.empty((counts.size, 3), np.uint8)
+    lib().mbo_colorize(_ptr(counts), counts.size, iter_max, _ptr(out))
+    return out

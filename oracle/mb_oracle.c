@@ -178,6 +178,28 @@ void mbo_naive_rows(uint32_t m, uint32_t workers, uint32_t r, uint32_t* first, u
 /* Alternating row partition (Sec. III-C): row i belongs to worker i mod N. */
 uint32_t mbo_alternating_owner(uint32_t i, uint32_t workers) { return i % workers; }
 
+/* Iteration -> pixel colour (Sec. I: the iteration determines the colour; the
+ * paper gives no palette).  Reading taken: points that never escape are
+ * black; otherwise each channel is a triangle wave of the count,
+ * tri(x) = x < 256 ? x : 511 - x, with r = tri((7k) mod 512),
+ * g = tri((5k) mod 512), b = tri((3k) mod 512).  Integers only. */
+static unsigned tri(unsigned x) { return x < 256u ? x : 511u - x; }
+
+void mbo_colorize(const uint32_t* counts, uint64_t count, uint32_t iter_max, uint8_t* rgb) {
+  for (uint64_t t = 0; t < count; t++) {
+    uint32_t k = counts[t];
+    uint8_t r = 0, g = 0, b = 0;
+    if (k != iter_max) {
+      r = (uint8_t)tri((uint32_t)(((uint64_t)k * 7u) % 512u));
+      g = (uint8_t)tri((uint32_t)(((uint64_t)k * 5u) % 512u));
+      b = (uint8_t)tri((uint32_t)(((uint64_t)k * 3u) % 512u));
+    }
+    rgb[3 * t] = r;
+    rgb[3 * t + 1] = g;
+    rgb[3 * t + 2] = b;
+  }
+}
+
 int mbo_max_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -358,3 +358,17 @@ class Server:
             self.destroy()
         except Exception:
             pass
+
+
+# ---- output ---------------------------------------------------------------------------
+
+def mb_colorize(counts, iter_max, rgb, stream=None):
+    """Palette colours (device uint8 tensor, 3 per pixel) of device counts."""
+    _check(_L().lib().mb_colorize(_ptr(counts), int(counts.numel()), int(iter_max), _ptr(rgb), _stream(stream)),
+           "mb_colorize")
+
+
+def mb_write_ppm(path, rgb_host, m, n):
+    """Binary PPM from host RGB bytes (numpy array or CPU tensor, m*n*3)."""
+    ptr = rgb_host.ctypes.data if hasattr(rgb_host, "ctypes") else rgb_host.data_ptr()
+    _check(_L().lib().mb_write_ppm(str(path).encode(), ptr, int(m), int(n)), "mb_write_ppm")

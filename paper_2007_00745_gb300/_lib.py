@@ -79,6 +79,10 @@ def _load():
     L.mb_fp64_peak.restype = i32
     L.mb_device_info.argtypes = [u32, ctypes.POINTER(u32), ctypes.POINTER(u32)]
     L.mb_selftest_products.argtypes = [vp, vp, u64, vp, vp, vp, vp]
+    L.mb_colorize.argtypes = [vp, u64, u32, vp, vp]
+    L.mb_colorize.restype = i32
+    L.mb_write_ppm.argtypes = [ctypes.c_char_p, vp, u32, u32]
+    L.mb_write_ppm.restype = i32
     L.mb_selftest_products.restype = i32
     L.mb_device_info.restype = i32
     P = ctypes.POINTER

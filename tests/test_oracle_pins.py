@@ -296,3 +296,10 @@ def test_tile_totals_and_probe_layout(orc):
     assert pr[0, 2, 3] == img[20, 28]
     assert pr[5, 7, 7] == img[99, 129]
     assert pr[4, 1, 0] == img[64 + 12, 64 + 4]
+
+
+def test_colour_palette_hand_values(orc):
+    # k = 1: (7, 5, 3); k = 40: 7*40=280 -> 511-280 = 231, 5*40=200, 3*40=120; k = iterMax: black;
+    # k = 73: 511 mod 512 -> tri(511) = 0, 365 -> 146, 219
+    rgb = orc.colorize(np.array([1, 40, 100, 73, 0], np.uint32), 100)
+    assert rgb.tolist() == [[7, 5, 3], [231, 200, 120], [0, 0, 0], [0, 146, 219], [0, 0, 0]]
