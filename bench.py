@@ -220,12 +220,12 @@ def pct(xs, q):
     return xs[k]
 
 
-def run_serve(mb, wl, torch, rate, count, seed_shift=0):
+def run_serve(mb, wl, torch, rate, count, seed_shift=0, **sopts):
     """Open-loop Poisson stream of batch-distribution viewports into a server with a
     40 GB budget; latency percentiles (submit to done) and delivered Giter/s."""
     views = wl.batch_views(count=count, seed=wl.SEED + 500 + seed_shift)
     arrivals = wl.poisson_arrivals(rate, count)
-    srv = mb.Server(budget_bytes=40 << 30, queue_limit=4096)
+    srv = mb.Server(budget_bytes=40 << 30, queue_limit=4096, **sopts)
     ids, lat, iters, failed = [None] * count, [], 0, 0
     tot = torch.zeros(1, dtype=torch.int64, device="cuda")
     side = torch.cuda.Stream()
@@ -371,6 +371,9 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / (peak / 1e12), "traffic": traffic,
                      "peak_source": "of measured: mb_fp64_peak, binary64 add/mul issue rate on this GPU now",
+                     "fp64_pipe_frac": 3.0 * render_iters / (kernel_ms * 1e-3) / peak,
+                     "fp64_pipe_note": "the kernel issues 3 binary64 additions per step on the FP64 pipe (the "
+                                       "products are exact on the integer pipes): 3 x steps/s over the measured peak",
                      "kernel": "render_kernel (main FCFS render, CUDA events around its launch)",
                      "algorithmic": "8 binary64 ops per escape step x %d steps per launch" % render_iters},
         "pct_fp64_peak": 100.0 * value * 1e9 * ALG_OPS_PER_ITER / peak,

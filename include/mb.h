@@ -96,6 +96,7 @@ typedef struct {
   void* workspace;           /* device, optional: temporary memory, >= mb_render_workspace_size() bytes, 256-byte aligned */
   size_t workspace_bytes;
   uint32_t split;            /* mb_render_learned: split divisor S of the order-and-split rule; 0 = 4 */
+  uint32_t round_tiles;      /* mb_serve_create: tiles per round; 0 = 16 x grid */
   uint32_t max_seconds;      /* 0 = no limit; else each CTA of the main render stops after running this long
                                 and ORs 4 into *status (a guard for interactive use; the image is then incomplete) */
   uint32_t fp64_products;    /* 1 = form the three products of a step on the FP64 pipe (MB_SCHED_FCFS_TILES
@@ -188,9 +189,9 @@ int mb_batch_autotune(const mb_view* views, uint32_t count, const mb_opts* base,
  * A request is one view; the server allocates its counts (m*n uint32) and Cx/Cy
  * arrays on the device, charging align256(m*n*4) + align256((m+n)*8) bytes to
  * the budget until the request is released.  Requests that do not fit yet wait
- * in a FIFO of at most queue_limit entries.  A worker thread keeps two rounds
- * in flight on two streams; each round is one FCFS render over the next tiles
- * of every admitted request (oldest first, at most 8 x grid tiles), so requests
+ * in a FIFO of at most queue_limit entries.  A worker thread keeps four rounds
+ * in flight on four streams; each round is one FCFS render over the next tiles
+ * of every admitted request (oldest first, at most round_tiles tiles), so requests
  * that arrive while others run join the next round and share the GPU.  Counts
  * are exactly those of mb_render.  Timestamps are host steady-clock ns. */
 typedef struct {
@@ -213,7 +214,7 @@ typedef struct {
 
 typedef struct mb_server mb_server;
 
-/* opts: tile (default 32), block (512), unroll (16), grid; other fields ignored.
+/* opts: tile (default 32), block (512), unroll (8), grid, round_tiles; other fields ignored.
  * queue_limit 0 = 1024. */
 int mb_serve_create(size_t mem_budget_bytes, uint32_t queue_limit, const mb_opts* opt, mb_server** s);
 /* MB_ENOMEM if the request alone exceeds the budget, MB_EBUSY if the queue is full. */

@@ -2,7 +2,7 @@
 //
 // Requests (one view each) are admitted while their device memory (counts,
 // Cx / Cy arrays) fits a byte budget; the rest wait in a bounded queue.  A
-// worker thread keeps up to two rounds in flight on two streams: each round is
+// worker thread keeps up to four rounds in flight on four streams: each round is
 // one first-come-first-served launch (Sec. III-B) over the next tiles of every
 // live request, oldest request first, so a request that arrives while others
 // are on the GPU joins the very next round and shares the machine with them.
@@ -60,7 +60,9 @@ struct Round {
 };
 
 constexpr uint32_t SERVE_SLOTS = 4096;
-constexpr int SERVE_STREAMS = 2;
+// Rounds in flight: a round that ends on a heavy tile holds its stream for a
+// while; with more rounds queued the other streams keep the GPU covered.
+constexpr int SERVE_STREAMS = 4;
 
 }  // namespace mb
 
@@ -82,8 +84,9 @@ struct mb_server {
   std::vector<uint32_t> free_slots;
   mb::ViewDesc* d_views = nullptr;
   mb::ViewDesc* h_view_stage = nullptr;  // pinned
-  cudaStream_t setup = nullptr, streams[mb::SERVE_STREAMS] = {nullptr, nullptr};
+  cudaStream_t setup = nullptr, streams[mb::SERVE_STREAMS] = {};
   cudaEvent_t setup_ev = nullptr;
+  cudaMemPool_t pool = nullptr;  // the server's own pool: freed request memory stays reserved for the next ones
   mb::Round rounds[mb::SERVE_STREAMS];
   mb::RenderFn fn_filt = nullptr, fn_exact = nullptr;
   mb_serve_counters ctr{};
@@ -102,7 +105,7 @@ static int admit_locked(mb_server* S) {
   while (!S->queue.empty() && !S->free_slots.empty()) {
     Req& R = S->reqs[S->queue.front()];
     if (S->in_use + R.bytes > S->budget) break;
-    if (cudaMallocAsync((void**)&R.dmem, R.bytes, S->setup) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync((void**)&R.dmem, R.bytes, S->pool, S->setup) != cudaSuccess) {
       cudaGetLastError();
       return MB_ECUDA;
     }
@@ -286,7 +289,7 @@ extern "C" int mb_serve_create(size_t mem_budget_bytes, uint32_t queue_limit, co
   if (opt) o = *opt;
   if (!o.tile) o.tile = 32;
   if (!o.block) o.block = 512;
-  if (!o.unroll) o.unroll = 16;
+  if (!o.unroll) o.unroll = 8;
   int rc = check_opts(&o, &log2_tile);
   if (rc) return rc;
   mb_server* S = new mb_server();
@@ -299,8 +302,17 @@ extern "C" int mb_serve_create(size_t mem_budget_bytes, uint32_t queue_limit, co
   S->fn_filt = render_fn(KIND_BATCH, S_FCFS, true, (int)S->unroll);
   S->fn_exact = render_fn(KIND_BATCH, S_FCFS, false, (int)S->unroll);
   S->grid = o.grid ? o.grid : default_grid(S->fn_filt, S->block);
-  S->round_tiles = 8 * S->grid;
-  bool ok = cudaMalloc((void**)&S->d_views, SERVE_SLOTS * sizeof(ViewDesc)) == cudaSuccess &&
+  S->round_tiles = o.round_tiles ? o.round_tiles : 16 * S->grid;
+  cudaMemPoolProps props;
+  std::memset(&props, 0, sizeof props);
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = S->device;
+  uint64_t keep = ~0ull;
+  bool ok = cudaMemPoolCreate(&S->pool, &props) == cudaSuccess &&
+            cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess &&
+            cudaMalloc((void**)&S->d_views, SERVE_SLOTS * sizeof(ViewDesc)) == cudaSuccess &&
             cudaMallocHost((void**)&S->h_view_stage, SERVE_SLOTS * sizeof(ViewDesc)) == cudaSuccess &&
             cudaStreamCreateWithFlags(&S->setup, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreateWithFlags(&S->setup_ev, cudaEventDisableTiming) == cudaSuccess;
@@ -489,6 +501,7 @@ extern "C" int mb_serve_destroy(mb_server* S) {
   if (S->setup) cudaStreamDestroy(S->setup);
   if (S->d_views) cudaFree(S->d_views);
   if (S->h_view_stage) cudaFreeHost(S->h_view_stage);
+  if (S->pool) cudaMemPoolDestroy(S->pool);
   delete S;
   return MB_OK;
 }

@@ -287,3 +287,36 @@ def test_real_axis_and_zero_column_replays(orc):
     for unroll in (4, 16):
         got = gpu_render(win, m, n, it, sched="fcfs_tiles", tile=16, unroll=unroll)["img"]
         assert np.array_equal(got, want)
+
+
+def test_caller_workspace(orc):
+    win, m, n, it = (-1.0, 0.5, -0.6, 0.6), 77, 131, 900
+    need = mb.mb_render_workspace_size(m, n)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    out = torch.empty(m * n, dtype=torch.int32, device="cuda")
+    mb.mb_render(win, m, n, it, 4.0, out, workspace=ws)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy().view(np.uint32).reshape(m, n), orc.render(win, m, n, it))
+    small = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(mb.MBError) as e:
+        mb.mb_render(win, m, n, it, 4.0, out, workspace=small)
+    assert e.value.code == 1
+
+
+def test_deadline_stops_a_long_launch_cleanly():
+    """A render far longer than max_seconds stops after about that long, reports
+    status bit 4, and leaves the context usable (a later render is correct)."""
+    win, m, n, it = (-0.3, 0.1, -0.3, 0.3), 8192, 8192, 200000   # all interior: ~1.3e13 steps, ~80 s
+    out = torch.empty(m * n, dtype=torch.int32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    mb.mb_render(win, m, n, it, 4.0, out, status=st, max_seconds=1)
+    b.record()
+    b.synchronize()
+    assert int(st.item()) & 4
+    assert a.elapsed_time(b) < 5000
+    small = torch.empty(64, dtype=torch.int32, device="cuda")
+    mb.mb_render((-2.0, 1.0, -1.0, 1.0), 8, 8, 100, 4.0, small)
+    torch.cuda.synchronize()
+    assert int(small.max().item()) == 100
