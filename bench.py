@@ -35,7 +35,7 @@ ALG_OPS_PER_ITER = 8  # binary64 operations per escape step: 3 mul, 1 doubling, 
 # profiles/render_kernel_list_8192x8192_it1000.md (dram read + write per launch
 # / pixels; traffic does not depend on iterMax, so it scales by pixel count);
 # used only while the kernel sources still hash to src_sha1, else null.
-NCU_RENDER = {"src_sha1": "13fed47939bee7c6748e020e666f7c69cf6c4247", "dram_bytes_per_pixel": 3.41}
+NCU_RENDER = {"src_sha1": "fbf9fa9ad68dab34960f330a533766cdabc9a857", "dram_bytes_per_pixel": 3.88}
 KERNEL_SOURCES = ("escape_core.cuh", "render_kernels.cuh")
 
 
@@ -447,6 +447,21 @@ def run_ours(args):
             st["giter_s"] = iters / (st["ms"] * 1e-3) / 1e9
             cmp[name] = st
         line["schedulers"] = cmp
+        # the small plain-method view (640 x 480, iterMax 1000, naive rows): launch-bound, reported as is
+        c1 = wl.FULL_VIEW_1
+        c1o = torch.empty(c1.m * c1.n, dtype=torch.int32, device=dev)
+        mb.mb_render(c1.window, c1.m, c1.n, c1.iter_max, c1.r2, c1o, sched="naive")
+        a, b = E(), E()
+        a.record(stream)
+        for _ in range(20):
+            mb.mb_render(c1.window, c1.m, c1.n, c1.iter_max, c1.r2, c1o, sched="naive", stream=stream)
+        b.record(stream)
+        b.synchronize()
+        c1ms = a.elapsed_time(b) / 20
+        mb.mb_sum_counts(c1o, total, stream=stream)
+        torch.cuda.synchronize()
+        line["config1_640x480"] = {"sched": "naive", "ms": c1ms, "iterations": int(total.item()),
+                                   "giter_s": int(total.item()) / (c1ms * 1e-3) / 1e9}
         if "naive" in cmp and "learned" in cmp:
             line["learned_vs_naive"] = {"speedup": cmp["naive"]["ms"] / cmp["learned"]["ms"],
                                         "makespan_ratio": cmp["learned"]["makespan_ms"] / cmp["naive"]["makespan_ms"]}

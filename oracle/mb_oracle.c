@@ -12,7 +12,7 @@
  * What it computes (Sec. I, Eq. 1 and Eq. 2 of the paper): for every pixel
  * (i, j) of an m x n image, iterate f(z) = z^2 + c from z = 0 and record the
  * iteration at which |z|^2 first exceeds the escape radius, or iterationMax.
- * Readings of points the paper leaves open (each listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - pixel -> c (Sec. I says only that c comes from m and n; Sec. III-A
  *     says every task precomputes the Cx and Cy arrays):
  *         c_re = xmin + (j * (xmax - xmin)) / n

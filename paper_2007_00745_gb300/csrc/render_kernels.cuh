@@ -134,6 +134,12 @@ __device__ uint32_t claim(const RenderParams& P, unsigned long long* word, uint3
     uint32_t it = (uint32_t)(w >> 32), o = (uint32_t)w;
     if (it == END_ITEM) return 0;
     uint32_t Pn = item_pixels<KIND>(P, it);
+    if (Pn == 0 && o == 0) {  // an empty item (rows = 0 in a list): its unique first claimer moves on
+      uint32_t nx = next_item<SCHED>(P, it);
+      if (nx != END_ITEM) atomicAdd(taken, 1u);
+      atomicExch(word, (unsigned long long)nx << 32);
+      continue;
+    }
     if (o < Pn) {
       item = it;
       off = o;

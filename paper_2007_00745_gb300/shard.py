@@ -5,8 +5,8 @@ path shards with no exchange step: tile t goes to GPU t mod G (the alternating
 scheme of Sec. III-C one level up), or, for a learned longest-first list, the
 list is dealt round-robin so that every GPU gets a share of the heavy head.
 Each GPU renders its tiles into its own memory; gathering the slices (the
-paper's master gather) is left to the caller.  On one-GPU machines the benchmark
-runs replicas instead.
+paper's master gather) is left to the caller.  On a single-GPU machine the
+benchmark runs replicas instead.
 """
 
 

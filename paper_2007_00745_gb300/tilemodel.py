@@ -64,12 +64,17 @@ def default_model(train_views=32, side=1024, tile=64, epochs=40, stream=None, ca
     path = os.path.join(CACHE_DIR, "tile_model_%s.bin" % key)
     params = torch.empty(mb.MB_MLP_PARAMS, dtype=torch.float32, device="cuda")
     if cache and os.path.exists(path):
-        mb.mb_model_load(path, params)
-        return params, None
+        try:
+            mb.mb_model_load(path, params)
+            return params, None
+        except mb.MBError:
+            pass   # unreadable or foreign file: train afresh
     X, y = build_training_set(wl.training_zoom_views(train_views, side), tile, stream=stream)
     params, loss = train(X, y, epochs=epochs, stream=stream)
     if cache:
         os.makedirs(CACHE_DIR, exist_ok=True)
         torch.cuda.synchronize()
-        mb.mb_model_save(params, path)
+        tmp = "%s.%d.tmp" % (path, os.getpid())   # several processes may train at once
+        mb.mb_model_save(params, tmp)
+        os.replace(tmp, path)
     return params, loss

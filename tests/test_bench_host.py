@@ -1,0 +1,32 @@
+"""Host-side arithmetic of the benchmark: makespan and idle tail from per-CTA
+trace records, and percentiles."""
+import numpy as np
+
+import bench
+
+
+def _trace(rows):
+    tr = np.zeros((len(rows), 3), np.int64)
+    for k, (s, e, sm) in enumerate(rows):
+        tr[k] = (s, e, sm)
+    return tr
+
+
+def test_trace_stats_idle_tail():
+    # two SMs, makespan 100 ns: SM 0 ends at 100, SM 1 at 60 -> idle tail (0 + 40) / (2 * 100)
+    st = bench.trace_stats(_trace([(0, 100, 0), (10, 60, 1), (0, 50, 1)]), 2)
+    assert st["makespan_ms"] == 100 / 1e6
+    assert st["idle_tail"] == 0.2
+
+
+def test_trace_stats_ignores_unwritten_records_and_missing_sms():
+    st = bench.trace_stats(_trace([(5, 105, 0), (0, 0, 0)]), 2)
+    assert st["makespan_ms"] == 100 / 1e6
+    assert st["idle_tail"] == 0.5     # SM 1 never ran anything
+
+
+def test_percentiles():
+    xs = list(range(1, 101))
+    assert bench.pct(xs, 50) in (50, 51)
+    assert bench.pct(xs, 99) == 99 or bench.pct(xs, 99) == 100
+    assert bench.pct([], 50) is None

@@ -320,3 +320,31 @@ def test_deadline_stops_a_long_launch_cleanly():
     mb.mb_render((-2.0, 1.0, -1.0, 1.0), 8, 8, 100, 4.0, small)
     torch.cuda.synchronize()
     assert int(small.max().item()) == 100
+
+
+def test_items_list_with_empty_and_bad_entries(orc):
+    """Empty items (rows = 0) are skipped; an item reaching past its tile is
+    reported in status bit 2 and its out-of-tile rows are not written."""
+    win, m, n, it = (-1.5, 0.5, -1.0, 1.0), 64, 64, 300
+    tile = 32
+    items = []
+    for t in range(4):
+        items.append((t, 0, 0))          # empty
+        items.append((t, 0, 16))
+        items.append((t, 16, 16))
+    arr = np.zeros((len(items), 2), np.int32)
+    for k, (t, r0, rows) in enumerate(items):
+        arr[k, 0] = t
+        arr[k, 1] = r0 | (rows << 16)
+    got = gpu_render(win, m, n, it, sched="fcfs_items", tile=tile, items=torch.from_numpy(arr).cuda(),
+                     n_items=len(items))["img"]
+    assert np.array_equal(got, orc.render(win, m, n, it))
+    bad = np.array([[0, 24 | (16 << 16)]], np.int32)   # rows 24..39 of a 32-row tile
+    out = torch.full((m * n,), -1, dtype=torch.int32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    mb.mb_render(win, m, n, it, 4.0, out, sched="fcfs_items", tile=tile, items=torch.from_numpy(bad).cuda(),
+                 n_items=1, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) & 2
+    img = out.cpu().numpy().reshape(m, n)
+    assert (img[24:32, :32] >= 0).all() and (img[32:, :] == -1).all()
