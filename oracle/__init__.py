@@ -42,6 +42,16 @@ def lib():
         L.mbo_alternating_owner.restype = u32
         L.mbo_max_threads.restype = i32
         L.mbo_colorize.argtypes = [p, u64, u32, p]
+        f32, pf = ctypes.c_float, ctypes.POINTER(ctypes.c_float)
+        L.mbo_escape_f32.argtypes = [f64, f64, u32, f64]
+        L.mbo_escape_f32.restype = u32
+        L.mbo_escape_df.argtypes = [f64, f64, u32, f64]
+        L.mbo_escape_df.restype = u32
+        for name in ("mbo_two_sum", "mbo_fast_two_sum", "mbo_two_prod"):
+            getattr(L, name).argtypes = [f32, f32, pf, pf]
+        for name in ("mbo_df_add4", "mbo_df_mul4"):
+            getattr(L, name).argtypes = [f32, f32, f32, f32, pf, pf]
+        L.mbo_render_rows_lowp.argtypes = [f64, f64, f64, f64, u32, u32, u32, f64, i32, u32, u32, p, i32]
         _lib = L
     return _lib
 
@@ -137,3 +147,52 @@ def colorize(counts, iter_max):
     out = np.empty((counts.size, 3), np.uint8)
     lib().mbo_colorize(_ptr(counts), counts.size, iter_max, _ptr(out))
     return out
+
+
+PRECISIONS = {"fp32": 1, "dfloat": 2}
+
+
+def escape_lowp(cr, ci, iter_max, r2=4.0, precision="fp32"):
+    """Escape count of one point in binary32 ("fp32") or double-float ("dfloat")."""
+    f = lib().mbo_escape_f32 if precision == "fp32" else lib().mbo_escape_df
+    return int(f(float(cr), float(ci), int(iter_max), float(r2)))
+
+
+def render_lowp(window, m, n, iter_max, r2=4.0, precision="fp32", row0=0, nrows=None, threads=0):
+    """Rows [row0, row0 + nrows) of the image in a reduced precision, uint32."""
+    nrows = m - row0 if nrows is None else nrows
+    out = np.empty((nrows, n), np.uint32)
+    lib().mbo_render_rows_lowp(*map(float, window), m, n, iter_max, float(r2), PRECISIONS[precision],
+                               row0, nrows, _ptr(out), threads)
+    return out
+
+
+def _f32_pair(fn, *args):
+    a, b = ctypes.c_float(), ctypes.c_float()
+    fn(*[float(x) for x in args], ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def two_sum(a, b):
+    """(s, e) with s + e == a + b exactly (binary32 inputs)."""
+    return _f32_pair(lib().mbo_two_sum, a, b)
+
+
+def fast_two_sum(a, b):
+    """(s, e) with s + e == a + b exactly when |a| >= |b|."""
+    return _f32_pair(lib().mbo_fast_two_sum, a, b)
+
+
+def two_prod(a, b):
+    """(p, e) with p + e == a * b exactly."""
+    return _f32_pair(lib().mbo_two_prod, a, b)
+
+
+def df_add(x, y):
+    """Double-float sum of (xh, xl) and (yh, yl)."""
+    return _f32_pair(lib().mbo_df_add4, x[0], x[1], y[0], y[1])
+
+
+def df_mul(x, y):
+    """Double-float product of (xh, xl) and (yh, yl)."""
+    return _f32_pair(lib().mbo_df_mul4, x[0], x[1], y[0], y[1])

@@ -10,7 +10,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "mb_oracle.c")
+SRCS = [os.path.join(HERE, "mb_oracle.c"), os.path.join(HERE, "mb_oracle_lowp.c")]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmb_oracle.so")
 
@@ -22,10 +22,10 @@ def build(force: bool = False) -> str:
     """Build the oracle library if missing or stale; return its path."""
     os.makedirs(OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
+            and all(os.path.getmtime(LIB) >= os.path.getmtime(s) for s in SRCS)):
         return LIB
     tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = ["gcc"] + FLAGS + ["-o", tmp, SRC]
+    cmd = ["gcc"] + FLAGS + ["-o", tmp] + SRCS + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB
