@@ -35,8 +35,8 @@ ALG_OPS_PER_ITER = 8  # binary64 operations per escape step: 3 mul, 1 doubling, 
 # profiles/render_kernel_list_8192x8192_it1000.md (dram read + write per launch
 # / pixels; traffic does not depend on iterMax, so it scales by pixel count);
 # used only while the kernel sources still hash to src_sha1, else null.
-NCU_RENDER = {"src_sha1": "fbf9fa9ad68dab34960f330a533766cdabc9a857", "dram_bytes_per_pixel": 3.88}
-KERNEL_SOURCES = ("escape_core.cuh", "render_kernels.cuh")
+NCU_RENDER = {"src_sha1": "f38909f14e676416b11f740922cf1a93a56ddb8d", "dram_bytes_per_pixel": 3.86}
+KERNEL_SOURCES = ("escape_core.cuh", "escape_lowp.cuh", "render_kernels.cuh")
 
 
 def parse():
@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--no-compare", action="store_true", help="skip the per-scheduler comparison")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-precision", action="store_true", help="skip the binary32 / double-float variants")
     p.add_argument("--zoom", action="store_true", help="add the 16384^2 deep-zoom comparison (about a minute)")
     p.add_argument("--table2", action="store_true",
                    help="add the GPU analogue of the paper's Table II: speed-up over one worker (CTA) of the "
@@ -262,6 +263,54 @@ def run_serve(mb, wl, torch, rate, count, seed_shift=0, **sopts):
             "budget_gb": 40 * 2 ** 30 / 1e9}
 
 
+# FP32-pipe operations per escape step of the reduced-precision lanes: binary32 =
+# 3 multiplies, 1 doubling, 4 adds; double-float = 3 double-word products
+# (9 each), 4 double-word sums (20 each), 2 adds for the doubling.
+LOWP_OPS_PER_STEP = {"fp32": 8, "dfloat": 109}
+FP32_LANES_PER_SM = 128
+
+
+def precision_variants(mb, v, ref, stream, clocks, args):
+    """Binary32 and double-float renders of the headline view: each variant's
+    own throughput (its own iteration count), the fraction of the FP32 pipe it
+    keeps busy, and how many pixels differ from the binary64 image `ref`."""
+    import torch
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    sms, _ = mb.mb_device_info(args.block)
+    mhz = clocks.get("sm_mhz") or 2070.0
+    lo = torch.empty_like(ref)
+    total = torch.zeros(1, dtype=torch.int64, device=ref.device)
+    res = {}
+    for prec in ("fp32", "dfloat"):
+        runs = {}
+        for sched, tile in (("fcfs_rows", 64), ("fcfs_tiles", 16)):
+            for unroll in (8, 16):
+                kw = dict(sched=sched, tile=tile, block=args.block, unroll=unroll, precision=prec, stream=stream)
+                mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, lo, **kw)
+                a, b = E(), E()
+                a.record(stream)
+                mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, lo, **kw)
+                b.record(stream)
+                b.synchronize()
+                runs["%s_u%d" % (sched, unroll)] = a.elapsed_time(b)
+        mb.mb_sum_counts(lo, total, stream=stream)
+        torch.cuda.synchronize()
+        iters = int(total.item())
+        differ = int((lo != ref).sum().item())
+        cls = int(((lo == v.iter_max) != (ref == v.iter_max)).sum().item())
+        best = min(runs, key=runs.get)
+        steps_s = iters / (runs[best] * 1e-3)
+        res[prec] = {"best": best, "ms": runs[best], "giter_s": steps_s / 1e9, "iterations": iters,
+                     "ms_by_launch": runs, "fp32_ops_per_step": LOWP_OPS_PER_STEP[prec],
+                     "fp32_pipe_frac": steps_s * LOWP_OPS_PER_STEP[prec] / (sms * FP32_LANES_PER_SM * mhz * 1e6),
+                     "pixels_differing_from_fp64": differ / ref.numel(),
+                     "interior_exterior_disagree": cls / ref.numel()}
+    res["note"] = ("not the paper's method: counts are exact for each variant's own operation sequence "
+                   "(parity tests) and differ from binary64 on the fraction shown; fp32_pipe_frac uses "
+                   "%d SMs x %d lanes at the sampled SM clock" % (sms, FP32_LANES_PER_SM))
+    return res
+
+
 def run_ours(args):
     import torch
 
@@ -466,6 +515,9 @@ def run_ours(args):
             line["learned_vs_naive"] = {"speedup": cmp["naive"]["ms"] / cmp["learned"]["ms"],
                                         "makespan_ratio": cmp["learned"]["makespan_ms"] / cmp["naive"]["makespan_ms"]}
 
+    if not args.no_precision:
+        line["precision_variants"] = precision_variants(mb, v, out, stream, clocks, args)
+
     if not args.no_batch:
         views = wl.batch_views(256)
         outs = [torch.empty(q.m * q.n, dtype=torch.int32, device=dev) for q in views]
@@ -532,6 +584,23 @@ def run_ours(args):
         for k in zc:
             zc[k]["giter_s"] = zi / (zc[k]["ms"] * 1e-3) / 1e9
         line["zoom16384"] = {"iterations": zi, "variants": zc}
+        if not args.no_precision:   # the reduced-precision variants on the deep zoom (pixel spacing 6e-10)
+            zl = torch.empty_like(zo)
+            lowp = {}
+            for prec in ("dfloat", "fp32"):
+                a, b = E(), E()
+                a.record()
+                mb.mb_render(z.window, z.m, z.n, z.iter_max, z.r2, zl, sched="fcfs_tiles", tile=16,
+                             block=args.block, unroll=16, precision=prec)
+                b.record()
+                b.synchronize()
+                mb.mb_sum_counts(zl, total)
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b)
+                lowp[prec] = {"ms": ms, "giter_s": int(total.item()) / (ms * 1e-3) / 1e9,
+                              "iterations": int(total.item()),
+                              "pixels_differing_from_fp64": float((zl != zo).float().mean().item())}
+            line["zoom16384"]["precision_variants"] = lowp
 
     if args.table2:
         from paper_2007_00745_gb300 import report

@@ -63,6 +63,29 @@ typedef enum {
   MB_SCHED_FCFS_ITEMS = 4    /* as FCFS_TILES, over a caller-given device list of mb_item (e.g. longest-first) */
 } mb_sched;
 
+/* Arithmetic of the escape step (mb_opts.precision).  Only MB_PREC_FP64 is the
+ * paper's method and bit-identical to the binary64 evaluation above.  The other
+ * two trade count accuracy for throughput; each is defined by its exact
+ * operation sequence, with the same per-iteration order:
+ *  - MB_PREC_FP32: c_re, c_im and R2 are the binary64 values rounded once to
+ *    binary32 (nearest-even); every operation is then one binary32 operation.
+ *  - MB_PREC_DFLOAT: double-float.  A value is an unevaluated sum h + l of two
+ *    binary32 numbers; a binary64 x becomes h = RN32(x), l = RN32(x - h).
+ *    Sums use the accurate double-word sum and products the double-word product
+ *    with three fused multiply-adds (Joldes, Muller, Popescu, ACM TOMS 44(2),
+ *    2017: relative errors below 3u^2 and 4u^2, u = 2^-24).  2*x doubles both
+ *    parts, and the escape test compares (h, l) pairs lexicographically.
+ * Their counts differ from binary64 on some pixels near the set's boundary
+ * (binary32 on a few per mille of a full view at iterMax 1000, double-float on a
+ * few per hundred thousand).  The difference grows with zoom depth and
+ * iterMax, and binary32 stops resolving pixels once the pixel spacing nears
+ * 2^-24 |c|.  The paper has no counterpart: it computes in double precision. */
+typedef enum {
+  MB_PREC_FP64 = 0,
+  MB_PREC_FP32 = 1,
+  MB_PREC_DFLOAT = 2
+} mb_precision;
+
 /* One work item of MB_SCHED_FCFS_ITEMS: rows [row0, row0+rows) of tile `tile`
  * (tiles numbered row-major, tile x tile pixels, cut at the image edge). */
 typedef struct {
@@ -103,6 +126,9 @@ typedef struct {
                                 only; a measured baseline), 0 = exactly on the integer pipes (default) */
   void* ev_start;            /* cudaEvent_t, optional: recorded on the stream right before the main render kernel */
   void* ev_stop;             /* cudaEvent_t, optional: recorded right after it (to time that kernel alone) */
+  uint32_t precision;        /* mb_precision; 0 = MB_PREC_FP64.  Other values are accepted by mb_render only
+                                (any scheduler; not with fp64_products); every other entry point returns
+                                MB_EINVAL for them */
 } mb_opts;
 
 /* Library version string. */
@@ -117,7 +143,8 @@ const char* mb_strerror(int code);
  *   iter_max iteration budget per pixel (0 allowed: every count is 0)
  *   escape_r2  squared escape radius R^2, finite and > 0
  *   out      device, m*n uint32, written in full
- *   opt      host, may be NULL (all defaults)
+ *   opt      host, may be NULL (all defaults); opt->precision selects binary64 (default,
+ *            the paper's method, bit-exact) or a reduced-precision variant (mb_precision)
  * Errors: MB_EINVAL for bad arguments; MB_ENOMEM / MB_ECUDA from the launch. */
 int mb_render(const mb_window* w, uint32_t m, uint32_t n, uint32_t iter_max, double escape_r2,
               uint32_t* out, const mb_opts* opt);
@@ -128,7 +155,7 @@ int mb_render(const mb_window* w, uint32_t m, uint32_t n, uint32_t iter_max, dou
 /* The paper has no counterpart to this entry point; it exists for callers that
  * must not allocate device memory.  It renders exactly what mb_render renders
  * (same arguments, same counts, same options except `workspace`, which must be
- * NULL), but calls no cudaMalloc / cudaMallocAsync / cudaFree: the temporary
+ * NULL, and `precision`, which must be MB_PREC_FP64), but calls no cudaMalloc / cudaMallocAsync / cudaFree: the temporary
  * memory it needs sits in one fixed array inside the library's device image
  * (262,656 bytes, resident on every GPU that loads the library until exit).
  * Typical callers: code running where the allocator may not be entered (host

@@ -15,6 +15,8 @@ __all__ = [
 MB_SCHED_NAIVE, MB_SCHED_ALTERNATING, MB_SCHED_FCFS_ROWS, MB_SCHED_FCFS_TILES, MB_SCHED_FCFS_ITEMS = range(5)
 SCHEDS = {"naive": MB_SCHED_NAIVE, "alternating": MB_SCHED_ALTERNATING, "fcfs_rows": MB_SCHED_FCFS_ROWS,
           "fcfs_tiles": MB_SCHED_FCFS_TILES, "fcfs_items": MB_SCHED_FCFS_ITEMS}
+MB_PREC_FP64, MB_PREC_FP32, MB_PREC_DFLOAT = range(3)
+PRECISIONS = {"fp64": MB_PREC_FP64, "fp32": MB_PREC_FP32, "dfloat": MB_PREC_DFLOAT}
 
 
 def _L():
@@ -49,7 +51,7 @@ def _stream(stream):
 
 def _opts(sched="fcfs_tiles", tile=0, grid=0, block=0, unroll=0, stream=None, items=None, n_items=0,
           tile_totals=None, trace=None, trace_len=0, status=None, workspace=None, workspace_bytes=0,
-          events=None, fp64_products=0, max_seconds=300, split=0, round_tiles=0):
+          events=None, fp64_products=0, max_seconds=300, split=0, round_tiles=0, precision="fp64"):
     L = _L()
     o = L.mb_opts()
     o.sched = SCHEDS[sched] if isinstance(sched, str) else int(sched)
@@ -66,6 +68,7 @@ def _opts(sched="fcfs_tiles", tile=0, grid=0, block=0, unroll=0, stream=None, it
     o.max_seconds = int(max_seconds)
     o.split = int(split)
     o.round_tiles = int(round_tiles)
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     if events is not None:   # (start, stop) torch.cuda.Event pair recorded around the main render kernel
         handles = []
         for ev in events:

@@ -176,6 +176,19 @@ __device__ __forceinline__ void lane_start(Lane& L, double cr, double ci, uint32
   L.pend = false;
 }
 
+// Same, with the escape radius of the view (used by the reduced-precision lanes).
+__device__ __forceinline__ void lane_start(Lane& L, double cr, double ci, uint32_t lim, double) {
+  lane_start(L, cr, ci, lim);
+}
+
+// An idle lane.
+__device__ __forceinline__ void lane_clear(Lane& L) {
+  L.zr = L.zi = L.cr = L.ci = L.szr = L.szi = 0.0;
+  L.cnt = L.lim = L.scnt = 0;
+  L.live = false;
+  L.pend = false;
+}
+
 // Checkpoint at the start of a block of steps.
 __device__ __forceinline__ void block_begin(Lane& L) {
   L.szr = L.zr;

@@ -48,7 +48,7 @@ int check_view(const mb_window* w, uint32_t m, uint32_t n, double r2, const void
   return MB_OK;
 }
 
-int check_opts(const mb_opts* o, uint32_t* log2_tile) {
+int check_opts(const mb_opts* o, uint32_t* log2_tile, bool allow_lowp) {
   uint32_t tile = o && o->tile ? o->tile : DEFAULT_TILE;
   if (tile < 8 || tile > 256 || (tile & (tile - 1))) return MB_EINVAL;
   uint32_t l = 0;
@@ -60,6 +60,9 @@ int check_opts(const mb_opts* o, uint32_t* log2_tile) {
   if (o && o->sched == MB_SCHED_FCFS_ITEMS && (!o->items || o->n_items == 0)) return MB_EINVAL;
   if (o && o->workspace && (((uintptr_t)o->workspace) & 255)) return MB_EINVAL;
   if (o && o->unroll && o->unroll != 4 && o->unroll != 8 && o->unroll != 16) return MB_EINVAL;
+  if (o && o->precision != MB_PREC_FP64) {
+    if (!allow_lowp || o->precision > MB_PREC_DFLOAT || o->fp64_products) return MB_EINVAL;
+  }
   return MB_OK;
 }
 
@@ -171,7 +174,7 @@ extern "C" int mb_render(const mb_window* w, uint32_t m, uint32_t n, uint32_t it
   int rc = check_view(w, m, n, escape_r2, out);
   if (rc) return rc;
   uint32_t log2_tile = 0;
-  rc = check_opts(opt, &log2_tile);
+  rc = check_opts(opt, &log2_tile, true);
   if (rc) return rc;
   const int sched = opt ? opt->sched : MB_SCHED_FCFS_TILES;
   const uint32_t block = opt && opt->block ? opt->block : DEFAULT_BLOCK;
@@ -230,7 +233,9 @@ extern "C" int mb_render(const mb_window* w, uint32_t m, uint32_t n, uint32_t it
     case MB_SCHED_FCFS_ITEMS: kind = KIND_LIST; s = S_FCFS; P.n_items = opt->n_items; P.items = opt->items; break;
     default: kind = KIND_RASTER; s = S_FCFS; P.n_items = tiles_x * tiles_y; break;
   }
-  RenderFn fn = render_fn(kind, s, filter_ok(escape_r2), opt_unroll(opt));
+  const int prec = opt ? (int)opt->precision : PREC_F64;
+  RenderFn fn = prec == PREC_F64 ? render_fn(kind, s, filter_ok(escape_r2), opt_unroll(opt))
+                                 : render_fn_lowp(kind, s, prec, opt_unroll(opt));
   if (opt && opt->fp64_products) {
     if (kind != KIND_RASTER) {
       if (owned) cudaFreeAsync(ws, st);

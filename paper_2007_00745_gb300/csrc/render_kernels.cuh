@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "escape_core.cuh"
+#include "escape_lowp.cuh"
 #include "mb.h"
 #include "mb_internal.h"
 
@@ -216,7 +217,9 @@ __device__ __forceinline__ bool decode(const RenderParams& P, uint32_t it, uint3
   return ty < V.tiles_y && row < V.m && col < V.n;
 }
 
-template <int KIND, int SCHED, bool FILT, int UNROLL, bool EMUL>
+// PREC selects the lane arithmetic: the exact binary64 step (escape_core.cuh)
+// or a reduced-precision one (escape_lowp.cuh; FILT and EMUL then unused).
+template <int KIND, int SCHED, bool FILT, int UNROLL, bool EMUL, int PREC = PREC_F64>
 __global__ void __launch_bounds__(512) render_kernel(RenderParams P) {
   __shared__ unsigned long long s_word;
   __shared__ uint32_t s_taken;
@@ -232,11 +235,8 @@ __global__ void __launch_bounds__(512) render_kernel(RenderParams P) {
   }
   __syncthreads();
 
-  Lane L;
-  L.zr = L.zi = L.cr = L.ci = L.szr = L.szi = 0.0;
-  L.cnt = L.lim = L.scnt = 0;
-  L.live = false;
-  L.pend = false;
+  typename LaneOf<PREC>::type L;
+  lane_clear(L);
   bool has = false;
   bool drained = false;
   uint32_t* optr = nullptr;
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(512) render_kernel(RenderParams P) {
         uint32_t v, row, col, tile;
         if (decode<KIND>(P, item, off + rank, v, row, col, tile)) {
           const ViewDesc& V = P.views[v];
-          lane_start(L, V.cx[col], V.cy[row], V.iter_max);
+          lane_start(L, V.cx[col], V.cy[row], V.iter_max, V.r2);
           r2 = V.r2;
           thr = V.thr;
           optr = V.out ? V.out + (size_t)row * V.n + col : nullptr;
