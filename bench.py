@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-precision", action="store_true", help="skip the binary32 / double-float variants")
+    p.add_argument("--no-cycle", action="store_true", help="skip the exact-cycle-detection timing")
     p.add_argument("--zoom", action="store_true", help="add the 16384^2 deep-zoom comparison (about a minute)")
     p.add_argument("--table2", action="store_true",
                    help="add the GPU analogue of the paper's Table II: speed-up over one worker (CTA) of the "
@@ -311,6 +312,34 @@ def precision_variants(mb, v, ref, stream, clocks, args):
     return res
 
 
+def cycle_variant(mb, v, ref, stream, args):
+    """Time to the same binary64 image with exact cycle detection (mb_opts.cycle_check)
+    against the same launch without it.  Reported as time only: the detected
+    pixels' remaining steps do not run, so a Giter/s figure would count steps
+    that were never executed."""
+    import torch
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    got = torch.empty_like(ref)
+    res = {}
+    for name, kw in (("fcfs_rows", dict(sched="fcfs_rows", tile=64)), ("fcfs_tiles16", dict(sched="fcfs_tiles", tile=16))):
+        t = {}
+        for cyc in (0, 1):
+            kws = dict(kw, block=args.block, unroll=args.unroll, stream=stream, cycle_check=cyc)
+            mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, got, **kws)
+            a, b = E(), E()
+            a.record(stream)
+            mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, got, **kws)
+            b.record(stream)
+            b.synchronize()
+            t[cyc] = a.elapsed_time(b)
+        res[name] = {"ms_full_iteration": t[0], "ms_cycle_check": t[1], "speedup": t[0] / t[1],
+                     "same_image": bool(torch.equal(got, ref))}
+    res["note"] = ("exact shortcut, not in the paper: a pixel whose binary64 state repeats bit for bit at a "
+                   "block start is periodic and never escapes, so it gets iterMax at once; the image is "
+                   "identical (same_image) and only time is reported")
+    return res
+
+
 def run_ours(args):
     import torch
 
@@ -517,6 +546,8 @@ def run_ours(args):
 
     if not args.no_precision:
         line["precision_variants"] = precision_variants(mb, v, out, stream, clocks, args)
+    if not args.no_cycle:
+        line["cycle_check"] = cycle_variant(mb, v, out, stream, args)
 
     if not args.no_batch:
         views = wl.batch_views(256)

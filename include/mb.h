@@ -129,6 +129,11 @@ typedef struct {
   uint32_t precision;        /* mb_precision; 0 = MB_PREC_FP64.  Other values are accepted by mb_render only
                                 (any scheduler; not with fp64_products); every other entry point returns
                                 MB_EINVAL for them */
+  uint32_t cycle_check;      /* 1 = stop a pixel as soon as its binary64 state (zr, zi) at the start of a block of
+                                steps equals, bit for bit, its state at an earlier block start (kept at blocks
+                                1, 2, 4, 8, ...): the orbit is then periodic and never escapes, so the count is
+                                iterMax.  Counts are identical to cycle_check = 0; fewer steps run.  Not in the
+                                paper.  mb_render only, binary64 only (not with fp64_products); 0 = off */
 } mb_opts;
 
 /* Library version string. */

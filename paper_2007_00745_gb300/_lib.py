@@ -33,7 +33,8 @@ class mb_opts(ctypes.Structure):
     _fields_ = [("sched", i32), ("tile", u32), ("grid", u32), ("block", u32), ("unroll", u32),
                 ("stream", vp), ("items", vp), ("n_items", u32), ("tile_totals", vp), ("trace", vp), ("trace_len", u32),
                 ("status", vp), ("workspace", vp), ("workspace_bytes", sz), ("split", u32), ("round_tiles", u32), ("max_seconds", u32), ("fp64_products", u32),
-                ("ev_start", vp), ("ev_stop", vp), ("precision", u32)]
+                ("ev_start", vp), ("ev_stop", vp), ("precision", u32),
+                ("cycle_check", u32)]
 
 
 class mb_view(ctypes.Structure):

@@ -196,6 +196,48 @@ __device__ __forceinline__ void block_begin(Lane& L) {
   L.scnt = L.cnt;
 }
 
+// A lane that also detects exactly periodic orbits.  If the binary64 state
+// (zr, zi) at the start of a block is bit-identical to the state at an earlier
+// block start, the map -- a fixed sequence of rounded operations on that state
+// and the same c -- repeats the same steps forever; none of them escaped the
+// first time, so none ever will, and the count is iterMax.  The state is
+// compared at block starts (where it is exact: resolve() has run) against a
+// copy saved at blocks 1, 2, 4, 8, ... of the pixel (Brent's power-of-two
+// schedule), which finds any cycle within about twice its pre-period plus
+// period.  Counts are unchanged; only steps are saved.
+struct LaneCyc : Lane {
+  double pzr, pzi;  // state saved at the last power-of-two block
+  uint32_t blk;     // blocks begun since the pixel started
+};
+
+__device__ __forceinline__ void lane_clear(LaneCyc& L) {
+  lane_clear(static_cast<Lane&>(L));
+  L.pzr = L.pzi = 0.0;
+  L.blk = 0;
+}
+
+__device__ __forceinline__ void lane_start(LaneCyc& L, double cr, double ci, uint32_t lim, double) {
+  lane_start(static_cast<Lane&>(L), cr, ci, lim);
+  L.pzr = L.zr;
+  L.pzi = L.zi;
+  L.blk = 0;
+}
+
+__device__ __forceinline__ void block_begin(LaneCyc& L) {
+  bool rep = L.blk != 0u && __double_as_longlong(L.zr) == __double_as_longlong(L.pzr) &&
+             __double_as_longlong(L.zi) == __double_as_longlong(L.pzi);
+  if (rep && L.live) {
+    L.cnt = L.lim;
+    L.live = false;
+  }
+  L.blk += 1u;
+  if ((L.blk & (L.blk - 1u)) == 0u) {
+    L.pzr = L.zr;
+    L.pzi = L.zi;
+  }
+  block_begin(static_cast<Lane&>(L));
+}
+
 // One step for one lane; straight-line code.  FILT selects the FP32 escape
 // filter (R2 in [2^-100, 2^100]); otherwise the test is the literal binary64
 // add and compare.  EMUL selects the integer-pipe products (else three FP64

@@ -204,5 +204,9 @@ template <>
 struct LaneOf<PREC_F2> {
   using type = LaneF2;
 };
+template <>
+struct LaneOf<PREC_F64_CYCLE> {
+  using type = LaneCyc;
+};
 
 }  // namespace mb

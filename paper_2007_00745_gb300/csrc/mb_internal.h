@@ -18,8 +18,9 @@ enum ItemKind : int { KIND_ROWS = 0, KIND_RASTER = 1, KIND_LIST = 2, KIND_BATCH 
 // tile-local pixel (a*s + s/2, b*s + s/2), s = tile / PROBE_SIDE, clamped to the image).
 constexpr uint32_t PROBE_SIDE = 8;
 enum SchedKind : int { S_NAIVE = 0, S_ALT = 1, S_FCFS = 2 };
-// Arithmetic of the escape step (values of mb_opts.precision).
-enum Precision : int { PREC_F64 = 0, PREC_F32 = 1, PREC_F2 = 2 };
+// Arithmetic of the escape step: the values of mb_opts.precision, and binary64
+// with exact cycle detection (mb_opts.cycle_check).
+enum Precision : int { PREC_F64 = 0, PREC_F32 = 1, PREC_F2 = 2, PREC_F64_CYCLE = 3 };
 
 struct RenderParams;
 struct EscThr;
@@ -28,12 +29,14 @@ using RenderFn = void (*)(RenderParams);
 bool filter_ok(double r2);
 EscThr make_thr(double r2);
 int check_view(const mb_window* w, uint32_t m, uint32_t n, double r2, const void* out);
-// allow_lowp: the entry point honours mb_opts.precision (else it must be 0)
-int check_opts(const mb_opts* o, uint32_t* log2_tile, bool allow_lowp = false);
+// variants: the entry point honours mb_opts.precision and cycle_check (else both must be 0)
+int check_opts(const mb_opts* o, uint32_t* log2_tile, bool variants = false);
 RenderFn render_fn(int kind, int sched, bool filt, int unroll);
 RenderFn render_fn_fp64(bool filt);
 // binary32 / double-float kernels (render_lowp.cu): KIND_ROWS, KIND_RASTER and KIND_LIST
 RenderFn render_fn_lowp(int kind, int sched, int prec, int unroll);
+// binary64 kernels with exact cycle detection (render_cycle.cu): KIND_ROWS, KIND_RASTER and KIND_LIST
+RenderFn render_fn_cycle(int kind, int sched, bool filt, int unroll);
 int launch_render(const RenderFn fn, const RenderParams& P, uint32_t grid, uint32_t block, cudaStream_t st);
 // launch_render with the caller's optional timing events around it (opts->ev_start / ev_stop)
 int launch_render_timed(const RenderFn fn, const RenderParams& P, uint32_t grid, uint32_t block, cudaStream_t st,

@@ -48,7 +48,7 @@ int check_view(const mb_window* w, uint32_t m, uint32_t n, double r2, const void
   return MB_OK;
 }
 
-int check_opts(const mb_opts* o, uint32_t* log2_tile, bool allow_lowp) {
+int check_opts(const mb_opts* o, uint32_t* log2_tile, bool variants) {
   uint32_t tile = o && o->tile ? o->tile : DEFAULT_TILE;
   if (tile < 8 || tile > 256 || (tile & (tile - 1))) return MB_EINVAL;
   uint32_t l = 0;
@@ -61,7 +61,10 @@ int check_opts(const mb_opts* o, uint32_t* log2_tile, bool allow_lowp) {
   if (o && o->workspace && (((uintptr_t)o->workspace) & 255)) return MB_EINVAL;
   if (o && o->unroll && o->unroll != 4 && o->unroll != 8 && o->unroll != 16) return MB_EINVAL;
   if (o && o->precision != MB_PREC_FP64) {
-    if (!allow_lowp || o->precision > MB_PREC_DFLOAT || o->fp64_products) return MB_EINVAL;
+    if (!variants || o->precision > MB_PREC_DFLOAT || o->fp64_products) return MB_EINVAL;
+  }
+  if (o && o->cycle_check) {
+    if (!variants || o->cycle_check != 1 || o->precision != MB_PREC_FP64 || o->fp64_products) return MB_EINVAL;
   }
   return MB_OK;
 }
@@ -234,8 +237,9 @@ extern "C" int mb_render(const mb_window* w, uint32_t m, uint32_t n, uint32_t it
     default: kind = KIND_RASTER; s = S_FCFS; P.n_items = tiles_x * tiles_y; break;
   }
   const int prec = opt ? (int)opt->precision : PREC_F64;
-  RenderFn fn = prec == PREC_F64 ? render_fn(kind, s, filter_ok(escape_r2), opt_unroll(opt))
-                                 : render_fn_lowp(kind, s, prec, opt_unroll(opt));
+  RenderFn fn = prec != PREC_F64       ? render_fn_lowp(kind, s, prec, opt_unroll(opt))
+                : opt && opt->cycle_check ? render_fn_cycle(kind, s, filter_ok(escape_r2), opt_unroll(opt))
+                                          : render_fn(kind, s, filter_ok(escape_r2), opt_unroll(opt));
   if (opt && opt->fp64_products) {
     if (kind != KIND_RASTER) {
       if (owned) cudaFreeAsync(ws, st);
