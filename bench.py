@@ -7,7 +7,9 @@ tile features, MLP cost prediction, longest-first order with splits, and the
 FCFS render of the rest -- with every count bit-identical to the FP64 oracle.
 Giter/s = (sum of counts, i.e. z-updates) / step time.  The roofline is the
 FP64 pipe, measured in this run by the library's own microbenchmark
-(mb_fp64_peak), against the nominal 8 binary64 operations per escape step.
+(mb_fp64_peak): a step's 8 nominal binary64 operations take 3 FP64-pipe
+issues (the products are formed exactly on the integer pipes), so the
+attainable rate is the measured issue rate x 8/3.
 
 Beside the headline (outside the timed region, rank 0 only): the paper's three
 row schedulers and plain tile FCFS on the same view (makespan, idle tail), the
@@ -30,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 ALG_OPS_PER_ITER = 8  # binary64 operations per escape step: 3 mul, 1 doubling, 4 add/sub
+FP64_PIPE_OPS_PER_ITER = 3  # of which issued on the FP64 pipe: the 3 additions (products on the integer pipes)
 
 # DRAM traffic of the main render kernel from the ncu capture summarised in
 # profiles/render_kernel_list_8192x8192_it1000.md (dram read + write per launch
@@ -312,6 +315,29 @@ def precision_variants(mb, v, ref, stream, clocks, args):
     return res
 
 
+def roofline_entry(steps, kernel_ms, peak, traffic):
+    """Roofline of the main render launch: `steps` escape steps in `kernel_ms`,
+    against the FP64-pipe issue rate `peak` (binary64 ops/s) measured in this run.
+    The binding pipe is FP64, which each step uses for its 3 additions only, so
+    the attainable rate of the step's 8 nominal binary64 ops is peak x 8/3."""
+    step_peak = peak * ALG_OPS_PER_ITER / FP64_PIPE_OPS_PER_ITER
+    achieved = steps * ALG_OPS_PER_ITER / (kernel_ms * 1e-3)
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": step_peak / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / step_peak, "traffic": traffic,
+            "peak_source": ("derived from measured (of measured): the FP64-pipe issue rate measured now "
+                            "by mb_fp64_peak (%.4f T binary64 ops/s) x 8/3 -- each escape step's 8 "
+                            "nominal binary64 ops need 3 FP64-pipe issues (its additions); the three "
+                            "products run exactly on the integer pipes, which are not the binding "
+                            "pipe (ncu: FP64 84 %%, integer ALU 78 %% busy)" % (peak / 1e12)),
+            "fp64_pipe_frac": FP64_PIPE_OPS_PER_ITER * steps / (kernel_ms * 1e-3) / peak,
+            "nominal_frac": achieved / peak,
+            "nominal_note": "8 nominal ops per step over the plain FP64-pipe peak (the BASELINE "
+                            "'% of FP64 peak' form, above 1 because 5 of the 8 ops are not FP64-pipe "
+                            "instructions)",
+            "kernel": "render_kernel (main FCFS render, CUDA events around its launch)",
+            "algorithmic": "8 binary64 ops per escape step x %d steps per launch" % steps}
+
+
 def cycle_variant(mb, v, ref, stream, args):
     """Time to the same binary64 image with exact cycle detection (mb_opts.cycle_check)
     against the same launch without it.  Reported as time only: the detected
@@ -434,7 +460,6 @@ def run_ours(args):
 
     # roofline of the dominant kernel: the main render, timed by its own events
     render_iters = iters - probe_iters
-    achieved = render_iters * ALG_OPS_PER_ITER / (kernel_ms * 1e-3) / 1e12
     traffic = None
     if NCU_RENDER["src_sha1"] and NCU_RENDER["src_sha1"] == kernel_sha1():
         traffic = NCU_RENDER["dram_bytes_per_pixel"] * v.m * v.n
@@ -446,14 +471,7 @@ def run_ours(args):
                                % (v.m, v.n, v.iter_max, args.sched, args.tile, args.block, args.unroll),
                    "iterations_per_step": iters, "l2": "counts 268 MB per step > 129 MB L2 (compute-bound)",
                    "parallelism": "replicas" if ws > 1 else "1 GPU", "bit_exact": "vs FP64 oracle (tests)"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved / (peak / 1e12), "traffic": traffic,
-                     "peak_source": "of measured: mb_fp64_peak, binary64 add/mul issue rate on this GPU now",
-                     "fp64_pipe_frac": 3.0 * render_iters / (kernel_ms * 1e-3) / peak,
-                     "fp64_pipe_note": "the kernel issues 3 binary64 additions per step on the FP64 pipe (the "
-                                       "products are exact on the integer pipes): 3 x steps/s over the measured peak",
-                     "kernel": "render_kernel (main FCFS render, CUDA events around its launch)",
-                     "algorithmic": "8 binary64 ops per escape step x %d steps per launch" % render_iters},
+        "roofline": roofline_entry(render_iters, kernel_ms, peak, traffic),
         "pct_fp64_peak": 100.0 * value * 1e9 * ALG_OPS_PER_ITER / peak,
         "kernel_ms": kernel_ms,
         "clocks": clocks,

@@ -19,9 +19,11 @@
 // three fused multiply-adds (relative error below 4u^2).  2*x doubles both
 // parts; the escape test compares (h, l) pairs lexicographically.
 //
-// Neither variant needs the exactness machinery of the binary64 step, so
-// there is no replay: a lane simply counts while it has not escaped, and the
-// iteration budget is applied once per block of steps (see resolve()).
+// Neither variant needs the exactness machinery of the binary64 step.  The
+// iteration budget is applied once per block of steps (see resolve()): inside a
+// block a lane counts every non-escaping iteration even past iterMax; since the
+// count only grows while the orbit has not escaped, min(count, iterMax) is the
+// count the bounded loop would give.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -32,18 +34,28 @@
 namespace mb {
 
 // ---- binary32 ------------------------------------------------------------
+//
+// The binary32 step is so cheap that bookkeeping would cost as much as the
+// arithmetic, so a block of steps only ORs each step's escape test into one
+// flag (no per-step count).  Between blocks, a lane whose flag is clear just
+// adds the block's steps to its count; a lane whose flag is set replays the
+// block from its checkpoint with the same binary32 operations, one step at a
+// time, to find the exact escape step (once per pixel).
 
 struct LaneF32 {
   float zr, zi, cr, ci, r2;
+  float szr, szi;   // state at the start of the block
   uint32_t cnt, lim;
   bool live;
+  bool esc;         // some step of this block escaped
 };
 
 __device__ __forceinline__ void lane_clear(LaneF32& L) {
-  L.zr = L.zi = L.cr = L.ci = 0.0f;
+  L.zr = L.zi = L.cr = L.ci = L.szr = L.szi = 0.0f;
   L.r2 = 4.0f;
   L.cnt = L.lim = 0;
   L.live = false;
+  L.esc = false;
 }
 
 __device__ __forceinline__ void lane_start(LaneF32& L, double cr, double ci, uint32_t lim, double r2) {
@@ -55,33 +67,56 @@ __device__ __forceinline__ void lane_start(LaneF32& L, double cr, double ci, uin
   L.cnt = 0;
   L.lim = lim;
   L.live = lim != 0u;
+  L.esc = false;
 }
 
-__device__ __forceinline__ void block_begin(LaneF32&) {}
+__device__ __forceinline__ void block_begin(LaneF32& L) {
+  L.szr = L.zr;
+  L.szi = L.zi;
+  L.esc = false;
+}
 
-// One binary32 iteration.  A lane that has escaped keeps computing (its z runs
-// off to infinity) but no longer counts.
+// One binary32 iteration.  After an escape the lane keeps computing (its z runs
+// off to infinity); resolve() discards those steps.
+__device__ __forceinline__ void f32_iter(float& zr, float& zi, float cr, float ci, float r2, bool& esc) {
+  float zr2 = __fmul_rn(zr, zr);
+  float zi2 = __fmul_rn(zi, zi);
+  esc = __fadd_rn(zr2, zi2) > r2;
+  float t = __fmul_rn(__fadd_rn(zr, zr), zi);
+  zi = __fadd_rn(t, ci);
+  zr = __fadd_rn(__fsub_rn(zr2, zi2), cr);
+}
+
 template <bool FILT, bool EMUL>
 __device__ __forceinline__ void step(LaneF32& L, double, EscThr) {
-  float zr2 = __fmul_rn(L.zr, L.zr);
-  float zi2 = __fmul_rn(L.zi, L.zi);
-  bool esc = __fadd_rn(zr2, zi2) > L.r2;
-  L.live = L.live && !esc;
-  L.cnt += L.live ? 1u : 0u;
-  float t = __fmul_rn(__fadd_rn(L.zr, L.zr), L.zi);
-  L.zi = __fadd_rn(t, L.ci);
-  L.zr = __fadd_rn(__fsub_rn(zr2, zi2), L.cr);
+  bool e;
+  f32_iter(L.zr, L.zi, L.cr, L.ci, L.r2, e);
+  L.esc = L.esc || e;
 }
 
-// The budget, applied between blocks: inside a block a lane counts every
-// non-escaping iteration even past iterMax; since the count only grows while
-// the orbit has not escaped, min(count, iterMax) is the count the bounded loop
-// would give, and a lane that reached iterMax is done.
+// Settle a block: count it whole, or replay it to the escape; then apply the
+// budget (a lane that reached iterMax is done, with count iterMax).
 template <int STEPS>
 __device__ __forceinline__ void resolve(LaneF32& L, double) {
-  if (L.cnt >= L.lim) {
-    L.cnt = L.lim;
-    L.live = false;
+  if (L.live) {
+    if (L.esc) {
+      float zr = L.szr, zi = L.szi;
+      uint32_t c = L.cnt;
+      for (int k = 0; k < STEPS; ++k) {
+        bool e;
+        f32_iter(zr, zi, L.cr, L.ci, L.r2, e);
+        if (e) break;
+        ++c;
+      }
+      L.cnt = c;
+      L.live = false;
+    } else {
+      L.cnt += STEPS;
+    }
+    if (L.cnt >= L.lim) {
+      L.cnt = L.lim;
+      L.live = false;
+    }
   }
 }
 

@@ -30,3 +30,14 @@ def test_percentiles():
     assert bench.pct(xs, 50) in (50, 51)
     assert bench.pct(xs, 99) == 99 or bench.pct(xs, 99) == 100
     assert bench.pct([], 50) is None
+
+
+def test_roofline_entry_arithmetic():
+    # 1e11 steps in 600 ms against a 0.5 T ops/s FP64 pipe: 3 x 1e11 / 0.6 = 0.5e12 -> the pipe is full
+    r = bench.roofline_entry(100_000_000_000, 600.0, 0.5e12, None)
+    assert abs(r["fp64_pipe_frac"] - 1.0) < 1e-12
+    assert abs(r["frac"] - r["fp64_pipe_frac"]) < 1e-12
+    assert abs(r["peak"] - 0.5 * 8 / 3) < 1e-12
+    assert abs(r["achieved"] - 8e11 / 0.6 / 1e12) < 1e-12
+    assert abs(r["nominal_frac"] - 8 / 3 * r["frac"]) < 1e-12
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["traffic"] is None
