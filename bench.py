@@ -600,6 +600,12 @@ def run_ours(args):
 
     if not args.no_serve:
         line["serve"] = run_serve(mb, wl, torch, 50.0, args.serve_count)
+        if not args.no_cycle:   # the same request stream with exact cycle detection: latency only
+            sc = run_serve(mb, wl, torch, 50.0, args.serve_count, cycle_check=1)
+            sc["giter_s"] = None
+            sc["note"] = ("cycle_check=1: identical counts; detected pixels skip their remaining steps, so "
+                          "only latency and completions are reported")
+            line["serve_cycle_check"] = sc
     if args.serve_sweep:
         line["serve_sweep"] = [run_serve(mb, wl, torch, float(r), args.serve_count, k)
                                for k, r in enumerate(args.serve_sweep.split(","))]

@@ -133,7 +133,9 @@ typedef struct {
                                 steps equals, bit for bit, its state at an earlier block start (kept at blocks
                                 1, 2, 4, 8, ...): the orbit is then periodic and never escapes, so the count is
                                 iterMax.  Counts are identical to cycle_check = 0; fewer steps run.  Not in the
-                                paper.  mb_render only, binary64 only (not with fp64_products); 0 = off */
+                                paper.  Honoured by mb_render, mb_render_batch, mb_batch_plan_create and
+                                mb_serve_create (binary64 only, not with fp64_products); the other entry points
+                                return MB_EINVAL for it; 0 = off */
 } mb_opts;
 
 /* Library version string. */

@@ -29,13 +29,15 @@ using RenderFn = void (*)(RenderParams);
 bool filter_ok(double r2);
 EscThr make_thr(double r2);
 int check_view(const mb_window* w, uint32_t m, uint32_t n, double r2, const void* out);
-// variants: the entry point honours mb_opts.precision and cycle_check (else both must be 0)
-int check_opts(const mb_opts* o, uint32_t* log2_tile, bool variants = false);
+// Options an entry point honours beyond the common ones (check_opts rejects the others when set).
+enum OptAllow : unsigned { ALLOW_PRECISION = 1u, ALLOW_CYCLE = 2u };
+int check_opts(const mb_opts* o, uint32_t* log2_tile, unsigned allow = 0u);
 RenderFn render_fn(int kind, int sched, bool filt, int unroll);
 RenderFn render_fn_fp64(bool filt);
 // binary32 / double-float kernels (render_lowp.cu): KIND_ROWS, KIND_RASTER and KIND_LIST
 RenderFn render_fn_lowp(int kind, int sched, int prec, int unroll);
-// binary64 kernels with exact cycle detection (render_cycle.cu): KIND_ROWS, KIND_RASTER and KIND_LIST
+// binary64 kernels with exact cycle detection (render_cycle.cu): KIND_ROWS, KIND_RASTER, KIND_LIST
+// and KIND_BATCH; unroll 16, else 8
 RenderFn render_fn_cycle(int kind, int sched, bool filt, int unroll);
 int launch_render(const RenderFn fn, const RenderParams& P, uint32_t grid, uint32_t block, cudaStream_t st);
 // launch_render with the caller's optional timing events around it (opts->ev_start / ev_stop)

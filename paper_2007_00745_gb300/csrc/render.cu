@@ -48,7 +48,7 @@ int check_view(const mb_window* w, uint32_t m, uint32_t n, double r2, const void
   return MB_OK;
 }
 
-int check_opts(const mb_opts* o, uint32_t* log2_tile, bool variants) {
+int check_opts(const mb_opts* o, uint32_t* log2_tile, unsigned allow) {
   uint32_t tile = o && o->tile ? o->tile : DEFAULT_TILE;
   if (tile < 8 || tile > 256 || (tile & (tile - 1))) return MB_EINVAL;
   uint32_t l = 0;
@@ -61,10 +61,11 @@ int check_opts(const mb_opts* o, uint32_t* log2_tile, bool variants) {
   if (o && o->workspace && (((uintptr_t)o->workspace) & 255)) return MB_EINVAL;
   if (o && o->unroll && o->unroll != 4 && o->unroll != 8 && o->unroll != 16) return MB_EINVAL;
   if (o && o->precision != MB_PREC_FP64) {
-    if (!variants || o->precision > MB_PREC_DFLOAT || o->fp64_products) return MB_EINVAL;
+    if (!(allow & ALLOW_PRECISION) || o->precision > MB_PREC_DFLOAT || o->fp64_products) return MB_EINVAL;
   }
   if (o && o->cycle_check) {
-    if (!variants || o->cycle_check != 1 || o->precision != MB_PREC_FP64 || o->fp64_products) return MB_EINVAL;
+    if (!(allow & ALLOW_CYCLE) || o->cycle_check != 1 || o->precision != MB_PREC_FP64 || o->fp64_products)
+      return MB_EINVAL;
   }
   return MB_OK;
 }
@@ -177,7 +178,7 @@ extern "C" int mb_render(const mb_window* w, uint32_t m, uint32_t n, uint32_t it
   int rc = check_view(w, m, n, escape_r2, out);
   if (rc) return rc;
   uint32_t log2_tile = 0;
-  rc = check_opts(opt, &log2_tile, true);
+  rc = check_opts(opt, &log2_tile, ALLOW_PRECISION | ALLOW_CYCLE);
   if (rc) return rc;
   const int sched = opt ? opt->sched : MB_SCHED_FCFS_TILES;
   const uint32_t block = opt && opt->block ? opt->block : DEFAULT_BLOCK;

@@ -1,5 +1,6 @@
 // render_cycle.cu -- kernel table of the binary64 renders with exact cycle
-// detection (LaneCyc in escape_core.cuh) under the mb_render schedulers.
+// detection (LaneCyc in escape_core.cuh): the mb_render schedulers, and the
+// batched item list used by mb_render_batch and the server.
 #include "mb_internal.h"
 #include "render_kernels.cuh"
 
@@ -24,6 +25,7 @@ RenderFn render_fn_cycle(int kind, int sched, bool filt, int unroll) {
   }
   if (kind == KIND_RASTER) return pick_filt_cycle<KIND_RASTER, S_FCFS>(filt, unroll);
   if (kind == KIND_LIST) return pick_filt_cycle<KIND_LIST, S_FCFS>(filt, unroll);
+  if (kind == KIND_BATCH) return pick_filt_cycle<KIND_BATCH, S_FCFS>(filt, unroll);
   return nullptr;
 }
 

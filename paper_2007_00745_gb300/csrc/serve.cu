@@ -290,7 +290,7 @@ extern "C" int mb_serve_create(size_t mem_budget_bytes, uint32_t queue_limit, co
   if (!o.tile) o.tile = 32;
   if (!o.block) o.block = 512;
   if (!o.unroll) o.unroll = 8;
-  int rc = check_opts(&o, &log2_tile);
+  int rc = check_opts(&o, &log2_tile, ALLOW_CYCLE);
   if (rc) return rc;
   mb_server* S = new mb_server();
   S->budget = mem_budget_bytes;
@@ -299,8 +299,10 @@ extern "C" int mb_serve_create(size_t mem_budget_bytes, uint32_t queue_limit, co
   S->block = o.block;
   S->unroll = o.unroll;
   cudaGetDevice(&S->device);
-  S->fn_filt = render_fn(KIND_BATCH, S_FCFS, true, (int)S->unroll);
-  S->fn_exact = render_fn(KIND_BATCH, S_FCFS, false, (int)S->unroll);
+  S->fn_filt = o.cycle_check ? render_fn_cycle(KIND_BATCH, S_FCFS, true, (int)S->unroll)
+                             : render_fn(KIND_BATCH, S_FCFS, true, (int)S->unroll);
+  S->fn_exact = o.cycle_check ? render_fn_cycle(KIND_BATCH, S_FCFS, false, (int)S->unroll)
+                              : render_fn(KIND_BATCH, S_FCFS, false, (int)S->unroll);
   S->grid = o.grid ? o.grid : default_grid(S->fn_filt, S->block);
   S->round_tiles = o.round_tiles ? o.round_tiles : 16 * S->grid;
   cudaMemPoolProps props;

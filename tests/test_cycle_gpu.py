@@ -2,8 +2,9 @@
 repeats bit for bit at a block start is periodic, never escapes, and gets
 iterMax without running its remaining steps.  The counts must stay identical
 to the binary64 oracle (tolerance 0) under every scheduler and launch shape,
-on views full of interior points, on points with known cycles, and on the
-full-size view; the saving shows in the time."""
+on views full of interior points, on points with known cycles, in batches
+(one-shot and graph-replayed) and in the server, and on the full-size view;
+the saving shows in the time."""
 import numpy as np
 import pytest
 
@@ -94,7 +95,7 @@ def test_invalid_requests_are_rejected():
             mb.mb_render(w, m, n, 100, 4.0, out, **kw)
         assert e.value.code == 1
     with pytest.raises(mb.MBError):
-        mb.mb_render_batch([(w, m, n, 100, 4.0)], [out], cycle_check=1)
+        mb.mb_render_batch([(w, m, n, 100, 4.0)], [out], cycle_check=1, precision="fp32")
     with pytest.raises(mb.MBError):
         mb.mb_render_noalloc(w, m, n, 100, 4.0, out, cycle_check=1)
     with pytest.raises(mb.MBError):
@@ -129,3 +130,46 @@ def test_full_size_view_identical_and_faster(orc):
     for row0 in (1000, 4096, 5003):
         assert np.array_equal(img[row0:row0 + 2], orc.render_rows(v.window, v.m, v.n, v.iter_max, v.r2, row0, 2))
     assert t_cyc < 0.5 * t_full
+
+
+def _check_views(orc, vs, outs):
+    torch.cuda.synchronize()
+    for v, o in zip(vs, outs):
+        want = orc.render(v.window, v.m, v.n, v.iter_max, v.r2)
+        assert np.array_equal(o.cpu().numpy().view(np.uint32).reshape(v.m, v.n), want), v
+
+
+def _cycle_views():
+    vs = wl.batch_views(count=10, seed=wl.SEED + 55, side_range=(16, 300), iter_range=(100, 20000))
+    vs.append(wl.View((-2.0, 1.0, -1.5, 1.5), 90, 120, 8000))      # mostly interior and exterior
+    vs.append(wl.View((-1.30, -1.20, -0.05, 0.05), 33, 47, 12000))  # period-2 bulb
+    return vs
+
+
+def test_batch_with_cycle_check(orc):
+    vs = _cycle_views()
+    outs = [torch.full((v.m * v.n,), -1, dtype=torch.int32, device="cuda") for v in vs]
+    mb.mb_render_batch(vs, outs, tile=16, cycle_check=1)
+    _check_views(orc, vs, outs)
+    outs2 = [torch.full((v.m * v.n,), -1, dtype=torch.int32, device="cuda") for v in vs]
+    plan = mb.BatchPlan(vs, outs2, tile=32, block=512, unroll=16, cycle_check=1)
+    plan.launch()
+    plan.launch()   # a replay gives the same counts again
+    _check_views(orc, vs, outs2)
+    plan.destroy()
+
+
+def test_server_with_cycle_check(orc):
+    vs = _cycle_views()
+    srv = mb.Server(budget_bytes=1 << 28, cycle_check=1)
+    ids = [srv.submit(v) for v in vs]
+    outs = []
+    for rid, v in zip(ids, vs):
+        rc, _ = srv.wait(rid, 120000)
+        assert rc == 0, rc
+        t = torch.empty(v.m * v.n, dtype=torch.int32, device="cuda")
+        srv.read(rid, t)
+        srv.release(rid)
+        outs.append(t)
+    srv.destroy()
+    _check_views(orc, vs, outs)
