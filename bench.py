@@ -331,7 +331,7 @@ def roofline_entry(steps, kernel_ms, peak, traffic):
                             "pipe (ncu: FP64 84 %%, integer ALU 78 %% busy)" % (peak / 1e12)),
             "fp64_pipe_frac": FP64_PIPE_OPS_PER_ITER * steps / (kernel_ms * 1e-3) / peak,
             "nominal_frac": achieved / peak,
-            "nominal_note": "8 nominal ops per step over the plain FP64-pipe peak (the BASELINE "
+            "nominal_note": "8 nominal ops per step over the plain FP64-pipe peak (the metric's "
                             "'% of FP64 peak' form, above 1 because 5 of the 8 ops are not FP64-pipe "
                             "instructions)",
             "kernel": "render_kernel (main FCFS render, CUDA events around its launch)",

@@ -186,6 +186,34 @@ size_t mb_render_workspace_size(uint32_t m, uint32_t n, const mb_opts* opt);
  * i.e. the number of z-updates of a rendered image. */
 int mb_sum_counts(const uint32_t* counts, uint64_t count, uint64_t* total, void* stream);
 
+/* Statistics of one render launch (the per-worker accounting behind the paper's
+ * load-balance comparison of Sec. III-IV and Table II). */
+typedef struct {
+  uint64_t makespan_ns;   /* first CTA start to last CTA end of the main render launch (globaltimer) */
+  uint64_t iterations;    /* sum of the counts in the output buffer, i.e. z-updates of the image */
+  uint32_t ctas;          /* CTAs that wrote a record */
+  uint32_t sms;           /* SMs that ran at least one of them */
+  double idle_tail;       /* sum over the GPU's SMs of (makespan - that SM's last CTA end), over SMs x makespan */
+  double sm_busy_min;     /* per SM: (its last CTA end - its first CTA start) / makespan; min, mean, max */
+  double sm_busy_mean;
+  double sm_busy_max;
+} mb_run_stats;
+
+/* Statistics of the calling host thread's most recent mb_render or
+ * mb_render_learned call that launched its main render (mb_render_noalloc,
+ * batches and the server are not recorded; a call rejected with an error leaves
+ * the previous record).  Waits for that call's stream, then reads the per-CTA
+ * records -- the caller's opts->trace when given, else a small device buffer the
+ * library keeps per thread and device until the process exits -- and sums the
+ * counts of that call's output buffer, which must still hold them.  The stream of
+ * that call must still exist.  Renders one thread keeps in flight at once on
+ * several streams share that thread's buffer: pass opts->trace to each of them
+ * to keep their records apart.
+ *   st   host, filled in
+ * Errors: MB_EINVAL (st NULL), MB_ENOTFOUND (no render recorded on this thread, or
+ * its launch failed), MB_ECUDA. */
+int mb_last_stats(mb_run_stats* st);
+
 /* ---- batched mode: many viewports in one persistent launch ----
  * A view: window, size, iteration budget, R^2 and its own output buffer
  * (device, m*n uint32).  Each view is rendered exactly as mb_render would. */
@@ -382,6 +410,16 @@ int mb_fp64_peak(int op, double* ops_per_s, double* seconds);
  * kernels replay the step on the FP64 pipe instead.  Device arrays. */
 int mb_selftest_products(const double* a, const double* b, uint64_t n, double* sq, double* pr, uint8_t* ok,
                          void* stream);
+
+/* Self-test of the bounded wait in the work-claiming protocol (not in the
+ * paper; the failure-detection test of the render kernels).  Launches `ctas`
+ * CTAs of 4 warps in which the worker that should publish the next work item
+ * never does (its CTA's work word stays past the end of an item): every warp
+ * waits in the render kernels' own claim loop, gives up after its bounded spin
+ * (a fraction of a second), ORs 1 into *status and reports no work in
+ * got[ctas * 4] (device, uint32; 0 expected).  Asynchronous on `stream`; the
+ * context stays usable.  MB_EINVAL for NULL pointers or ctas outside [1, 1024]. */
+int mb_selftest_wait(uint32_t ctas, uint32_t* status, uint32_t* got, void* stream);
 
 /* Number of SMs and resident CTAs per SM the render kernel gets at `block` threads. */
 int mb_device_info(uint32_t block, uint32_t* sms, uint32_t* ctas_per_sm);

@@ -9,6 +9,7 @@ import ctypes
 
 __all__ = [
     "mb_version", "mb_strerror", "mb_render", "mb_render_noalloc", "mb_render_workspace_size", "mb_sum_counts",
+    "mb_last_stats",
     "mb_fp64_peak", "mb_device_info", "Window", "MBError",
 ]
 
@@ -138,6 +139,21 @@ def mb_sum_counts(counts, total, stream=None):
     """Sum of the uint32 counts in device tensor `counts` into device int64 tensor `total`."""
     _check(_L().lib().mb_sum_counts(_ptr(counts), int(counts.numel()), _ptr(total), _stream(stream)),
            "mb_sum_counts")
+
+
+def mb_last_stats():
+    """Statistics of this thread's most recent mb_render / mb_render_learned launch:
+    makespan_ns, iterations, ctas, sms, idle_tail, sm_busy_min/mean/max."""
+    L = _L()
+    st = L.mb_run_stats()
+    _check(L.lib().mb_last_stats(ctypes.byref(st)), "mb_last_stats")
+    return {f: getattr(st, f) for f, _ in L.mb_run_stats._fields_}
+
+
+def mb_selftest_wait(ctas, status, got, stream=None):
+    """Bounded-wait self-test of the work-claiming protocol (see mb.h)."""
+    L = _L()
+    _check(L.lib().mb_selftest_wait(int(ctas), _ptr(status), _ptr(got), _stream(stream)), "mb_selftest_wait")
 
 
 def mb_sum_counts_ptr(counts_ptr, count, total, stream=None):

@@ -55,6 +55,11 @@ class mb_serve_counters(ctypes.Structure):
                 ("bytes_in_use", u64), ("peak_bytes", u64), ("queued", u32)]
 
 
+class mb_run_stats(ctypes.Structure):
+    _fields_ = [("makespan_ns", u64), ("iterations", u64), ("ctas", u32), ("sms", u32), ("idle_tail", f64),
+                ("sm_busy_min", f64), ("sm_busy_mean", f64), ("sm_busy_max", f64)]
+
+
 class MBError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -76,6 +81,10 @@ def _load():
     L.mb_render_workspace_size.restype = sz
     L.mb_sum_counts.argtypes = [vp, u64, vp, vp]
     L.mb_sum_counts.restype = i32
+    L.mb_last_stats.argtypes = [ctypes.POINTER(mb_run_stats)]
+    L.mb_last_stats.restype = i32
+    L.mb_selftest_wait.argtypes = [u32, vp, vp, vp]
+    L.mb_selftest_wait.restype = i32
     L.mb_fp64_peak.argtypes = [i32, ctypes.POINTER(f64), ctypes.POINTER(f64)]
     L.mb_fp64_peak.restype = i32
     L.mb_device_info.argtypes = [u32, ctypes.POINTER(u32), ctypes.POINTER(u32)]

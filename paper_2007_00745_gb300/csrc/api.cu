@@ -1,10 +1,12 @@
 // api.cu -- small entry points: version, error names, count reduction, device
 // info and the FP64 issue-rate microbenchmark that defines "% of FP64 peak".
 #include <cstdint>
+#include <cstring>
 
 #include "mb.h"
 #include "mb_internal.h"
 #include "escape_core.cuh"
+#include "render_kernels.cuh"
 
 namespace mb {
 
@@ -56,9 +58,41 @@ __global__ void selftest_products_kernel(const double* __restrict__ a, const dou
   }
 }
 
+// Bounded-wait self-test of the CTA work-claiming protocol: the CTA's work word
+// says its item (a 64-pixel raster tile) is already claimed past its end, and
+// no worker will ever publish the next item -- the producer is gone.  Every warp
+// then runs the real claim() wait, which must give up after its bounded spin,
+// OR 1 into *status and report no work; got[warp] receives what claim()
+// returned (0 expected).  Nothing is read or written outside status and got.
+__global__ void selftest_wait_kernel(RenderParams P, uint32_t* got) {
+  __shared__ unsigned long long s_word;
+  __shared__ uint32_t s_taken;
+  if (threadIdx.x == 0) {
+    s_word = 65ull;  // item 0, next pixel 65 of 64
+    s_taken = 1u;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    uint32_t item = 0, off = 0;
+    uint32_t n = claim<KIND_RASTER, S_FCFS>(P, &s_word, &s_taken, 32u, item, off);
+    got[blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)] = n;
+  }
+}
+
 }  // namespace mb
 
 using namespace mb;
+
+extern "C" int mb_selftest_wait(uint32_t ctas, uint32_t* status, uint32_t* got, void* stream) {
+  if (!status || !got || ctas == 0 || ctas > 1024) return MB_EINVAL;
+  RenderParams P;
+  memset(&P, 0, sizeof P);
+  P.log2_tile = 3;  // raster items of 8 x 8 = 64 pixels; no view is read
+  P.n_items = 1;
+  P.status = status;
+  selftest_wait_kernel<<<ctas, 128, 0, (cudaStream_t)stream>>>(P, got);
+  return cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
+}
 
 extern "C" int mb_selftest_products(const double* a, const double* b, uint64_t n, double* sq, double* pr,
                                     uint8_t* ok, void* stream) {

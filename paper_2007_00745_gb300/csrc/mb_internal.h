@@ -47,6 +47,12 @@ uint32_t default_grid(RenderFn fn, uint32_t block);
 int sm_count();
 int resident_ctas(const void* fn, int block);
 
+// mb_last_stats bookkeeping (stats.cu): called right before the main render launch of
+// mb_render / mb_render_learned; gives P a trace buffer if the caller gave none.
+// stats_cancel() forgets the launch (call it when the launch failed).
+void stats_begin(RenderParams& P, uint32_t grid, cudaStream_t st, const uint32_t* counts, uint64_t npix);
+void stats_cancel();
+
 inline int opt_unroll(const mb_opts* o) { return o && o->unroll ? (int)o->unroll : (int)DEFAULT_UNROLL; }
 inline uint64_t opt_deadline_ns(const mb_opts* o) { return o && o->max_seconds ? o->max_seconds * 1000000000ull : 0ull; }
 

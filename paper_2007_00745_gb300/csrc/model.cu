@@ -698,7 +698,9 @@ extern "C" int mb_render_learned(const mb_window* w, uint32_t m, uint32_t n, uin
     PR.skip_probe = 1;
     PR.trace = opt ? opt->trace : nullptr;
     PR.trace_len = opt && opt->trace ? opt->trace_len : 0;
+    stats_begin(PR, grid, st, out, (uint64_t)m * n);
     rc = launch_render_timed(frender, PR, grid, block, st, opt);
+    if (rc != MB_OK) stats_cancel();
   }
   cudaFreeAsync(ws, st);
   return rc;

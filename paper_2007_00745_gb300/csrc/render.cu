@@ -254,7 +254,11 @@ extern "C" int mb_render(const mb_window* w, uint32_t m, uint32_t n, uint32_t it
   if (map_blocks > 1024) map_blocks = 1024;
   pixel_map_single_kernel<<<map_blocks, 256, 0, st>>>(V, (ViewDesc*)(ws + lay.view), P.counter);
   rc = cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
-  if (rc == MB_OK) rc = launch_render_timed(fn, P, grid, block, st, opt);
+  if (rc == MB_OK) {
+    stats_begin(P, grid, st, out, (uint64_t)m * n);
+    rc = launch_render_timed(fn, P, grid, block, st, opt);
+    if (rc != MB_OK) stats_cancel();
+  }
   if (owned) cudaFreeAsync(ws, st);
   return rc;
 }

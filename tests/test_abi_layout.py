@@ -22,6 +22,7 @@ STRUCTS = {
     "mb_request": _lib.mb_request,
     "mb_req_stats": _lib.mb_req_stats,
     "mb_serve_counters": _lib.mb_serve_counters,
+    "mb_run_stats": _lib.mb_run_stats,
 }
 
 
