@@ -38,7 +38,7 @@ FP64_PIPE_OPS_PER_ITER = 3  # of which issued on the FP64 pipe: the 3 additions 
 # profiles/render_kernel_list_8192x8192_it1000.md (dram read + write per launch
 # / pixels; traffic does not depend on iterMax, so it scales by pixel count);
 # used only while the kernel sources still hash to src_sha1, else null.
-NCU_RENDER = {"src_sha1": "f38909f14e676416b11f740922cf1a93a56ddb8d", "dram_bytes_per_pixel": 3.86}
+NCU_RENDER = {"src_sha1": "f43739b61e6855870fa994de50ee236b52a7199b", "dram_bytes_per_pixel": 3.86}
 KERNEL_SOURCES = ("escape_core.cuh", "escape_lowp.cuh", "render_kernels.cuh")
 
 
@@ -596,6 +596,20 @@ def run_ours(args):
                                      "iterMax log-U(256..65536), one persistent launch, CUDA graph replay",
                          "giter_s": bi / (bm * 1e-3) / 1e9, "ms": bm, "iterations": bi, "items": info["items"],
                          "pixels": info["pixels"], "autotuned": best, "autotune_sample_ms": tune_ms}
+        if not args.no_cycle:   # the same batch with exact cycle detection: time and identical counts only
+            couts = [torch.empty_like(o) for o in outs]
+            cplan = mb.BatchPlan(views, couts, cycle_check=1, **best)
+            cplan.launch()
+            a, b = E(), E()
+            a.record()
+            cplan.launch()
+            b.record()
+            b.synchronize()
+            cplan.destroy()
+            same = all(bool(torch.equal(x, y)) for x, y in zip(outs, couts))
+            line["batch"]["cycle_check"] = {"ms": a.elapsed_time(b), "speedup": bm / a.elapsed_time(b),
+                                            "same_counts": same}
+            del couts
         del outs
 
     if not args.no_serve:
@@ -656,6 +670,18 @@ def run_ours(args):
                               "iterations": int(total.item()),
                               "pixels_differing_from_fp64": float((zl != zo).float().mean().item())}
             line["zoom16384"]["precision_variants"] = lowp
+        if not args.no_cycle:   # exact cycle detection on the deep zoom: time and identical counts only
+            zc2 = torch.empty_like(zo)
+            a, b = E(), E()
+            a.record()
+            mb.mb_render(z.window, z.m, z.n, z.iter_max, z.r2, zc2, sched="fcfs_tiles", tile=16, block=args.block,
+                         cycle_check=1)
+            b.record()
+            b.synchronize()
+            line["zoom16384"]["cycle_check"] = {"ms": a.elapsed_time(b),
+                                                "speedup_vs_fcfs_tiles16": zc["fcfs_tiles16"]["ms"] / a.elapsed_time(b),
+                                                "same_counts": bool(torch.equal(zc2, zo))}
+            del zc2
 
     if args.table2:
         from paper_2007_00745_gb300 import report

@@ -115,6 +115,36 @@ def test_order_split_parity(ntiles, tile, grid, split):
     assert gl == om.order_and_split(y, tile, grid, split)
 
 
+@pytest.mark.parametrize("fill", [float("nan"), -0.5, 0.0, float("inf")])
+def test_order_split_unusable_predictions(fill):
+    """NaN / non-positive predictions give plain FCFS (raster order, no splits);
+    +inf saturates to the top level; the GPU matches the oracle in every case."""
+    ntiles, tile, grid = 1000, 64, 152
+    y = np.full(ntiles, fill, np.float32)
+    cap = ntiles * 16
+    items = torch.empty((cap, 2), dtype=torch.int32, device="cuda")
+    nit = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    mb.mb_order_split(torch.from_numpy(y).cuda(), ntiles, tile, grid, items, cap, nit, st)
+    torch.cuda.synchronize()
+    k = int(nit.item())
+    gl = [(int(a), int(b) & 0xFFFF, (int(b) >> 16) & 0xFFFF) for a, b in items[:k].cpu().numpy()]
+    assert gl == om.order_and_split(y, tile, grid, 4)
+    if not fill > 0:
+        assert gl == [(t, 0, tile) for t in range(ntiles)]
+
+
+def test_learned_render_with_a_broken_network_is_plain_fcfs(orc):
+    v = wl.View(wl.zoom_window(-0.74364, 0.13182, 3e-5, 200, 300), 200, 300, 3000)
+    params = torch.full((om.P_COUNT,), float("nan"), dtype=torch.float32, device="cuda")
+    out = torch.full((v.m * v.n,), -1, dtype=torch.int32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    mb.mb_render_learned(v.window, v.m, v.n, v.iter_max, v.r2, out, params, tile=32, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert np.array_equal(_u32(out).reshape(v.m, v.n), orc.render(v.window, v.m, v.n, v.iter_max, v.r2))
+
+
 @pytest.fixture(scope="module")
 def small_model():
     views = wl.training_zoom_views(8, 512, seed=wl.SEED + 101)

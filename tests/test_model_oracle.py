@@ -124,3 +124,17 @@ def test_order_and_split_invariants():
         if r0 == 0:
             firsts.append(t)
     assert firsts == sorted(range(500), key=lambda t: (-q[t], t))
+
+
+def test_unusable_predictions_fall_back_to_plain_fcfs():
+    """Predictions that are NaN, negative or zero all map to cost level 0: the
+    queue is then the tiles in raster order without splits, i.e. plain FCFS
+    over tiles -- the method without the model."""
+    for fill in (np.nan, -1.0, 0.0, -np.inf):
+        y = np.full(37, fill, np.float32)
+        assert M.order_and_split(y, 64, 8, 4) == [(t, 0, 64) for t in range(37)]
+    # a partly broken prediction only demotes the broken tiles (to the end, unsplit)
+    y = np.array([0.5, np.nan, 0.6], np.float32)
+    items = M.order_and_split(y, 64, 1000, 4)
+    assert list(dict.fromkeys(it[0] for it in items)) == [2, 0, 1]
+    assert items[-1] == (1, 0, 64)
