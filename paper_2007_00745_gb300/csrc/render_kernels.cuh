@@ -217,10 +217,11 @@ __device__ __forceinline__ bool decode(const RenderParams& P, uint32_t it, uint3
   return ty < V.tiles_y && row < V.m && col < V.n;
 }
 
-// PREC selects the lane arithmetic: the exact binary64 step (escape_core.cuh)
-// or a reduced-precision one (escape_lowp.cuh; FILT and EMUL then unused).
-template <int KIND, int SCHED, bool FILT, int UNROLL, bool EMUL, int PREC = PREC_F64>
-__global__ void __launch_bounds__(512) render_kernel(RenderParams P) {
+// The worker loop of every render kernel.  PREC selects the lane arithmetic:
+// the exact binary64 step (escape_core.cuh) or a reduced-precision one
+// (escape_lowp.cuh; FILT and EMUL then unused).
+template <int KIND, int SCHED, bool FILT, int UNROLL, bool EMUL, int PREC>
+__device__ __forceinline__ void render_body(RenderParams P) {
   __shared__ unsigned long long s_word;
   __shared__ uint32_t s_taken;
   __shared__ uint64_t s_t0;
@@ -306,6 +307,19 @@ __global__ void __launch_bounds__(512) render_kernel(RenderParams P) {
     rec.items = s_taken;
     P.trace[blockIdx.x] = rec;
   }
+}
+
+template <int KIND, int SCHED, bool FILT, int UNROLL, bool EMUL, int PREC = PREC_F64>
+__global__ void __launch_bounds__(512) render_kernel(RenderParams P) {
+  render_body<KIND, SCHED, FILT, UNROLL, EMUL, PREC>(P);
+}
+
+// Double-float lanes need about 50 registers; without a lower bound on resident
+// CTAs the compiler keeps them to 32 and spills.  Two 512-thread CTAs per SM
+// allow 64.
+template <int KIND, int SCHED, int UNROLL>
+__global__ void __launch_bounds__(512, 2) render_kernel_f2(RenderParams P) {
+  render_body<KIND, SCHED, false, UNROLL, false, PREC_F2>(P);
 }
 
 // Cx / Cy arrays of one or more views (Sec. III-A: every task precomputes them),

@@ -5,16 +5,12 @@
 
 namespace mb {
 
-template <int KIND, int SCHED, int PREC>
-static RenderFn pick_unroll_lowp(int unroll) {
-  return unroll == 16 ? render_kernel<KIND, SCHED, false, 16, false, PREC>
-                      : render_kernel<KIND, SCHED, false, 8, false, PREC>;
-}
-
 template <int KIND, int SCHED>
 static RenderFn pick_prec(int prec, int unroll) {
-  return prec == PREC_F32 ? pick_unroll_lowp<KIND, SCHED, PREC_F32>(unroll)
-                          : pick_unroll_lowp<KIND, SCHED, PREC_F2>(unroll);
+  if (prec == PREC_F32)
+    return unroll == 16 ? render_kernel<KIND, SCHED, false, 16, false, PREC_F32>
+                        : render_kernel<KIND, SCHED, false, 8, false, PREC_F32>;
+  return unroll == 16 ? render_kernel_f2<KIND, SCHED, 16> : render_kernel_f2<KIND, SCHED, 8>;
 }
 
 RenderFn render_fn_lowp(int kind, int sched, int prec, int unroll) {
