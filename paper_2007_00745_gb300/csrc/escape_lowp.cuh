@@ -37,10 +37,13 @@ namespace mb {
 //
 // The binary32 step is so cheap that bookkeeping would cost as much as the
 // arithmetic, so a block of steps only ORs each step's escape test into one
-// flag (no per-step count).  Between blocks, a lane whose flag is clear just
-// adds the block's steps to its count; a lane whose flag is set replays the
-// block from its checkpoint with the same binary32 operations, one step at a
-// time, to find the exact escape step (once per pixel).
+// flag (no per-step count), and each scheduling step runs F32_ITERS iterations
+// (a block of UNROLL steps is UNROLL * F32_ITERS iterations, which halves the
+// per-block overhead).  Between blocks, a lane whose flag is clear just adds
+// the block's iterations to its count; a lane whose flag is set replays the
+// block from its checkpoint with the same binary32 operations, one iteration
+// at a time, to find the exact escape (once per pixel).
+constexpr int F32_ITERS = 2;
 
 struct LaneF32 {
   float zr, zi, cr, ci, r2;
@@ -89,9 +92,12 @@ __device__ __forceinline__ void f32_iter(float& zr, float& zi, float cr, float c
 
 template <bool FILT, bool EMUL>
 __device__ __forceinline__ void step(LaneF32& L, double, EscThr) {
-  bool e;
-  f32_iter(L.zr, L.zi, L.cr, L.ci, L.r2, e);
-  L.esc = L.esc || e;
+#pragma unroll
+  for (int k = 0; k < F32_ITERS; ++k) {
+    bool e;
+    f32_iter(L.zr, L.zi, L.cr, L.ci, L.r2, e);
+    L.esc = L.esc || e;
+  }
 }
 
 // Settle a block: count it whole, or replay it to the escape; then apply the
@@ -102,7 +108,7 @@ __device__ __forceinline__ void resolve(LaneF32& L, double) {
     if (L.esc) {
       float zr = L.szr, zi = L.szi;
       uint32_t c = L.cnt;
-      for (int k = 0; k < STEPS; ++k) {
+      for (int k = 0; k < STEPS * F32_ITERS; ++k) {
         bool e;
         f32_iter(zr, zi, L.cr, L.ci, L.r2, e);
         if (e) break;
@@ -111,7 +117,7 @@ __device__ __forceinline__ void resolve(LaneF32& L, double) {
       L.cnt = c;
       L.live = false;
     } else {
-      L.cnt += STEPS;
+      L.cnt += STEPS * F32_ITERS;
     }
     if (L.cnt >= L.lim) {
       L.cnt = L.lim;
