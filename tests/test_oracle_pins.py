@@ -303,3 +303,18 @@ def test_colour_palette_hand_values(orc):
     # k = 73: 511 mod 512 -> tri(511) = 0, 365 -> 146, 219
     rgb = orc.colorize(np.array([1, 40, 100, 73, 0], np.uint32), 100)
     assert rgb.tolist() == [[7, 5, 3], [231, 200, 120], [0, 0, 0], [0, 146, 219], [0, 0, 0]]
+
+
+def test_row_band_and_pixel_list_agree_with_the_full_render(orc):
+    """render_rows and render_pixels (the bounded samples used at full size)
+    are slices of the pinned full render."""
+    win = (-0.8, -0.7, 0.05, 0.15)
+    img = orc.render(win, 77, 91, 2000)
+    assert np.array_equal(orc.render_rows(win, 77, 91, 2000, 4.0, 13, 9), img[13:22])
+    assert np.array_equal(orc.render_rows(win, 77, 91, 2000, 4.0, 76, 1), img[76:77])
+    rng = np.random.default_rng(9)
+    idx = rng.integers(0, 77 * 91, size=500).astype(np.uint64)
+    assert np.array_equal(orc.render_pixels(win, 77, 91, 2000, 4.0, idx), img.reshape(-1)[idx.astype(np.int64)])
+    cx, cy = orc.pixel_map(win, 77, 91)
+    assert cx[17] == orc.c_re(win, 91, 17) and cy[40] == orc.c_im(win, 77, 40)
+    assert img[40, 17] == orc.escape(cx[17], cy[40], 2000)
