@@ -17,6 +17,12 @@ MB_SCHED_NAIVE, MB_SCHED_ALTERNATING, MB_SCHED_FCFS_ROWS, MB_SCHED_FCFS_TILES, M
 SCHEDS = {"naive": MB_SCHED_NAIVE, "alternating": MB_SCHED_ALTERNATING, "fcfs_rows": MB_SCHED_FCFS_ROWS,
           "fcfs_tiles": MB_SCHED_FCFS_TILES, "fcfs_items": MB_SCHED_FCFS_ITEMS}
 MB_PREC_FP64, MB_PREC_FP32, MB_PREC_DFLOAT = range(3)
+
+# Per-launch time limit (mb_opts.max_seconds) used when a call does not pass one:
+# 0 = none, as in the C API.  A positive value makes each CTA of a render stop
+# after that many seconds and OR 4 into the status word (the image is then
+# incomplete); the test suite sets it as a guard.
+DEFAULT_MAX_SECONDS = 0
 PRECISIONS = {"fp64": MB_PREC_FP64, "fp32": MB_PREC_FP32, "dfloat": MB_PREC_DFLOAT}
 
 
@@ -52,7 +58,7 @@ def _stream(stream):
 
 def _opts(sched="fcfs_tiles", tile=0, grid=0, block=0, unroll=0, stream=None, items=None, n_items=0,
           tile_totals=None, trace=None, trace_len=0, status=None, workspace=None, workspace_bytes=0,
-          events=None, fp64_products=0, max_seconds=300, split=0, round_tiles=0, precision="fp64",
+          events=None, fp64_products=0, max_seconds=None, split=0, round_tiles=0, precision="fp64",
           cycle_check=0):
     L = _L()
     o = L.mb_opts()
@@ -67,7 +73,7 @@ def _opts(sched="fcfs_tiles", tile=0, grid=0, block=0, unroll=0, stream=None, it
                                                    if trace is not None and hasattr(trace, "numel") else 0))
     o.status = _ptr(status)
     o.fp64_products = int(fp64_products)
-    o.max_seconds = int(max_seconds)
+    o.max_seconds = int(DEFAULT_MAX_SECONDS if max_seconds is None else max_seconds)
     o.split = int(split)
     o.round_tiles = int(round_tiles)
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
