@@ -38,7 +38,7 @@ FP64_PIPE_OPS_PER_ITER = 3  # of which issued on the FP64 pipe: the 3 additions 
 # profiles/render_kernel_list_8192x8192_it1000.md (dram read + write per launch
 # / pixels; traffic does not depend on iterMax, so it scales by pixel count);
 # used only while the kernel sources still hash to src_sha1, else null.
-NCU_RENDER = {"src_sha1": "c1ca6b8e845754fda6d36cabaa3853a67a123f7f", "dram_bytes_per_pixel": 3.87}
+NCU_RENDER = {"src_sha1": "ad034a9e6145ab58af516ad0a2c137ed29937f18", "dram_bytes_per_pixel": 3.86}
 KERNEL_SOURCES = ("escape_core.cuh", "escape_lowp.cuh", "render_kernels.cuh")
 
 
@@ -315,6 +315,15 @@ def precision_variants(mb, v, ref, stream, clocks, args):
     return res
 
 
+def measured_hbm_gbs():
+    """Copy bandwidth of this GPU model from MEASURED_PEAKS.json at the repository root, if present."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError, TypeError):
+        return None
+
+
 def roofline_entry(steps, kernel_ms, peak, traffic):
     """Roofline of the main render launch: `steps` escape steps in `kernel_ms`,
     against the FP64-pipe issue rate `peak` (binary64 ops/s) measured in this run.
@@ -335,7 +344,10 @@ def roofline_entry(steps, kernel_ms, peak, traffic):
                             "'% of FP64 peak' form, above 1 because 5 of the 8 ops are not FP64-pipe "
                             "instructions)",
             "kernel": "render_kernel (main FCFS render, CUDA events around its launch)",
-            "algorithmic": "8 binary64 ops per escape step x %d steps per launch" % steps}
+            "algorithmic": "8 binary64 ops per escape step x %d steps per launch" % steps,
+            "dram_gbs": traffic / (kernel_ms * 1e-3) / 1e9 if traffic else None,
+            "dram_frac_of_measured_hbm": (traffic / (kernel_ms * 1e-3) / 1e9 / measured_hbm_gbs()
+                                          if traffic and measured_hbm_gbs() else None)}
 
 
 def cycle_variant(mb, v, ref, stream, args):

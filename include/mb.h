@@ -107,7 +107,9 @@ typedef struct {
   uint32_t tile;             /* tile side, a power of two in [8, 256]; 0 = 64 */
   uint32_t grid;             /* CTAs; 0 = SM count x resident CTAs per SM */
   uint32_t block;            /* threads per CTA, multiple of 32 in [32, 512]; 0 = 256 */
-  uint32_t unroll;           /* escape steps between lane refills: 4, 8 or 16; 0 = 8 */
+  uint32_t unroll;           /* escape steps between lane refills: 4, 8 or 16; 0 = 8.  The cycle-detection and
+                                reduced-precision kernels use 16 when 16 is asked, else 8; a binary32 step is
+                                four iterations */
   void* stream;              /* cudaStream_t; NULL = legacy default stream */
   const mb_item* items;      /* device; required for MB_SCHED_FCFS_ITEMS */
   uint32_t n_items;

@@ -41,3 +41,10 @@ def test_roofline_entry_arithmetic():
     assert abs(r["achieved"] - 8e11 / 0.6 / 1e12) < 1e-12
     assert abs(r["nominal_frac"] - 8 / 3 * r["frac"]) < 1e-12
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["traffic"] is None
+
+
+def test_roofline_dram_context(monkeypatch):
+    monkeypatch.setattr(bench, "measured_hbm_gbs", lambda: 5000.0)
+    r = bench.roofline_entry(1000, 500.0, 1e12, 2.5e8)   # 250 MB in 0.5 s = 0.5 GB/s
+    assert abs(r["dram_gbs"] - 0.5) < 1e-12 and abs(r["dram_frac_of_measured_hbm"] - 1e-4) < 1e-15
+    assert bench.roofline_entry(1000, 500.0, 1e12, None)["dram_gbs"] is None
