@@ -88,7 +88,7 @@ void mbo_render(double xmin, double xmax, double ymin, double ymax, uint32_t m, 
   (void)threads;
 }
 
-/* Rows [row0, row0 + nrows) of the image only (for bounded CPU samples). */
+/* Rows [row0, row0 + nrows) of the image of Eq. 2 only (for bounded CPU samples). */
 void mbo_render_rows(double xmin, double xmax, double ymin, double ymax, uint32_t m, uint32_t n,
                      uint32_t iter_max, double r2, uint32_t row0, uint32_t nrows, uint32_t* out,
                      int threads) {
@@ -107,7 +107,7 @@ void mbo_render_rows(double xmin, double xmax, double ymin, double ymax, uint32_
   (void)threads;
 }
 
-/* Counts of an arbitrary list of pixels, idx[t] = i * n + j. */
+/* Counts I_{i,j} (Eq. 2) of an arbitrary list of pixels, idx[t] = i * n + j. */
 void mbo_render_pixels(double xmin, double xmax, double ymin, double ymax, uint32_t m, uint32_t n,
                        uint32_t iter_max, double r2, const uint64_t* idx, size_t count,
                        uint32_t* out, int threads) {
@@ -123,7 +123,8 @@ void mbo_render_pixels(double xmin, double xmax, double ymin, double ymax, uint3
   (void)threads;
 }
 
-/* Sum of counts (z-updates) over each tile_h x tile_w tile; tiles are numbered
+/* Sum of counts (z-updates, Eq. 2) over each tile_h x tile_w tile -- the per-tile
+ * cost that the tile-cost model learns (not in the paper); tiles are numbered
  * row-major, the last tile row / column is cut at the image edge. */
 void mbo_tile_totals(const uint32_t* counts, uint32_t m, uint32_t n, uint32_t tile_h,
                      uint32_t tile_w, uint64_t* totals) {
@@ -135,7 +136,8 @@ void mbo_tile_totals(const uint32_t* counts, uint32_t m, uint32_t n, uint32_t ti
       totals[(i / tile_h) * tiles_x + (j / tile_w)] += counts[(size_t)i * n + j];
 }
 
-/* Low-resolution probe: in each tile x tile block, probe x probe samples, sample
+/* Low-resolution probe of Eq. 2 (the input of the tile-cost model; not in the
+ * paper): in each tile x tile block, probe x probe samples, sample
  * (a, b) at pixel (ty*tile + a*s + s/2, tx*tile + b*s + s/2) with s = tile/probe,
  * clamped to the last row / column of the image.  Output layout:
  * out[((ty * tiles_x + tx) * probe + a) * probe + b]. */
@@ -200,6 +202,7 @@ void mbo_colorize(const uint32_t* counts, uint64_t count, uint32_t iter_max, uin
   }
 }
 
+/* Host threads the OpenMP loops above use (the core count reported with the CPU baseline). */
 int mbo_max_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

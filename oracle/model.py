@@ -26,7 +26,9 @@ Adam (Kingma & Ba 2015):  m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
     p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)
 
 order and split (integers after one FP32 quantisation):
-    q_t = 0 if y_t <= 0 else min(int(float32(y_t) * float32(128)), 191)
+    q_t = 0 unless y_t > 0 (so NaN and non-positive predictions give 0: plain FCFS
+          order when the whole prediction is unusable), else
+          min(int(float32(y_t) * float32(128)), 191)
     tiles sorted by q descending, ties by tile index ascending (stable)
     c(q) = (2^(q >> 2) * M[q & 3]) >> 16,  M = [65536, 77936, 92682, 110218]
     target = max(1, (sum_t c(q_t)) // (S G))        G = number of CTAs, S the split
