@@ -39,10 +39,11 @@ namespace mb {
 // arithmetic, so a block of steps only ORs each step's escape test into one
 // flag (no per-step count), and each scheduling step runs F32_ITERS iterations
 // (a block of UNROLL steps is UNROLL * F32_ITERS iterations, which spreads the
-// per-block overhead over four times as many iterations).  Between blocks, a lane whose flag is clear just adds
-// the block's iterations to its count; a lane whose flag is set replays the
-// block from its checkpoint with the same binary32 operations, one iteration
-// at a time, to find the exact escape (once per pixel).
+// per-block overhead over four times as many iterations).  Between blocks, a
+// lane whose flag is clear just adds the block's iterations to its count; a
+// lane whose flag is set replays the block from its checkpoint with the same
+// binary32 operations, one iteration at a time, to find the exact escape (once
+// per pixel).
 constexpr int F32_ITERS = 4;
 
 struct LaneF32 {
