@@ -1,0 +1,87 @@
+"""Parity at full size, in the launch configurations bench.py times:
+
+* the 8192 x 8192, iterMax 10000 view through the learned pipeline with the
+  benchmark's trained model, tile 32, 512 threads, unroll 8;
+* the 16384 x 16384 deep zoom at iterMax 50000 through the learned order on
+  64-pixel tiles;
+* the 256-viewport batch as an autotuned, graph-replayed plan.
+
+Each is checked on sampled pixels against the oracle (which computes them one
+by one), and the two large views also against a second scheduler on the whole
+image (bit for bit) and, for the symmetric view, by exact conjugate symmetry.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2007_00745_gb300 as mb  # noqa: E402
+from paper_2007_00745_gb300 import tilemodel, workloads as wl  # noqa: E402
+
+
+def _samples(out, v, count, seed):
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(0, v.m * v.n, size=count, dtype=np.uint64)
+    got = out[torch.from_numpy(idx.astype(np.int64)).cuda()].cpu().numpy().view(np.uint32)
+    return idx, got
+
+
+@pytest.fixture(scope="module")
+def params():
+    p, _ = tilemodel.default_model()
+    torch.cuda.synchronize()
+    return p
+
+
+def test_headline_configuration(orc, params):
+    v = wl.FULL_VIEW_2
+    out = torch.full((v.m * v.n,), -1, dtype=torch.int32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    mb.mb_render_learned(v.window, v.m, v.n, v.iter_max, v.r2, out, params, tile=32, block=512, unroll=8, status=st)
+    ref = torch.empty_like(out)
+    mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, ref, sched="fcfs_tiles", tile=16, block=512)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert torch.equal(out, ref)
+    img = out.view(v.m, v.n)
+    assert torch.equal(img[1:], img.flip(0)[:-1])          # rows i and 8192 - i: exact conjugates
+    idx, got = _samples(out, v, 3000, 23)
+    assert np.array_equal(got, orc.render_pixels(v.window, v.m, v.n, v.iter_max, v.r2, idx))
+
+
+def test_deep_zoom_configuration(orc, params):
+    z = wl.ZOOM_3
+    out = torch.full((z.m * z.n,), -1, dtype=torch.int32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    mb.mb_render_learned(z.window, z.m, z.n, z.iter_max, z.r2, out, params, tile=64, block=512, unroll=8, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert int((out < 0).sum().item()) == 0                # every pixel written
+    idx, got = _samples(out, z, 2000, 29)
+    assert np.array_equal(got, orc.render_pixels(z.window, z.m, z.n, z.iter_max, z.r2, idx))
+    ref = torch.empty_like(out)
+    mb.mb_render(z.window, z.m, z.n, z.iter_max, z.r2, ref, sched="fcfs_tiles", tile=16, block=512)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+
+
+def test_batch_configuration(orc):
+    views = wl.batch_views(256)
+    outs = [torch.full((v.m * v.n,), -1, dtype=torch.int32, device="cuda") for v in views]
+    with tempfile.TemporaryDirectory() as d:
+        best, _ = mb.mb_batch_autotune(views, outs, sample_stride=8, cache_path=os.path.join(d, "cache.txt"))
+    plan = mb.BatchPlan(views, outs, **best)
+    plan.launch()
+    torch.cuda.synchronize()
+    plan.destroy()
+    for k, (v, o) in enumerate(zip(views, outs)):
+        idx, got = _samples(o, v, 12, 1000 + k)
+        assert np.array_equal(got, orc.render_pixels(v.window, v.m, v.n, v.iter_max, v.r2, idx)), k
+        assert int((o < 0).sum().item()) == 0
