@@ -85,3 +85,25 @@ def test_batch_configuration(orc):
         idx, got = _samples(o, v, 12, 1000 + k)
         assert np.array_equal(got, orc.render_pixels(v.window, v.m, v.n, v.iter_max, v.r2, idx)), k
         assert int((o < 0).sum().item()) == 0
+
+
+def test_serving_configuration(orc):
+    """Requests drawn from the serving workload's distribution (the batch
+    viewports: sides up to 4096, budgets up to 65536), submitted together to a
+    server with the benchmark's budget and queue, so that many are on the GPU at
+    once; each result is checked on sampled pixels against the oracle."""
+    views = wl.batch_views(count=40, seed=wl.SEED + 500)
+    srv = mb.Server(budget_bytes=40 << 30, queue_limit=4096)
+    ids = [srv.submit(v) for v in views]
+    for k, (rid, v) in enumerate(zip(ids, views)):
+        rc, _ = srv.wait(rid, 600000)
+        assert rc == 0, (k, rc)
+        out = torch.empty(v.m * v.n, dtype=torch.int32, device="cuda")
+        srv.read(rid, out)
+        srv.release(rid)
+        idx, got = _samples(out, v, 12, 2000 + k)
+        assert np.array_equal(got, orc.render_pixels(v.window, v.m, v.n, v.iter_max, v.r2, idx)), k
+        assert int((out < 0).sum().item()) == 0
+    c = srv.counters()
+    srv.destroy()
+    assert c["completed"] == 40 and c["bytes_in_use"] == 0
