@@ -13,9 +13,14 @@ attainable rate is the measured issue rate x 8/3.
 
 Beside the headline (outside the timed region, rank 0 only): the paper's three
 row schedulers and plain tile FCFS on the same view (makespan, idle tail), the
-end-to-end figure through host buffers, the CPU oracle on a row sample, the
-256-viewport batch as a replayed CUDA graph, and a short Poisson serving run
-(p50 / p99 latency).  --zoom adds the 16384^2 deep-zoom comparison.
+end-to-end figure through host buffers, the paper's computation / total timing
+with the PPM file, the 640 x 480 naive view, the binary32 and double-float
+variants (their own rates and how many pixels differ from binary64), exact
+cycle detection (time to the identical image), the CPU oracle on a row sample,
+the 256-viewport batch as a replayed CUDA graph, and a short Poisson serving
+run (p50 / p99 latency), plain and with cycle detection.  --zoom adds the
+16384^2 deep-zoom comparison, --table2 the GPU analogue of the paper's Table II
+and --serve-sweep a sweep of request rates.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
