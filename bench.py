@@ -355,6 +355,44 @@ def roofline_entry(steps, kernel_ms, peak, traffic):
                                           if traffic and measured_hbm_gbs() else None)}
 
 
+def spearman(a, b):
+    """Rank correlation of two 1-D arrays (ties broken by position)."""
+    import numpy as np
+    ra = np.empty(len(a)); ra[np.argsort(a, kind="stable")] = np.arange(len(a))
+    rb = np.empty(len(b)); rb[np.argsort(b, kind="stable")] = np.arange(len(b))
+    return float(np.corrcoef(ra, rb)[0, 1])
+
+
+def model_quality(mb, v, params, tile, stream):
+    """How well the trained network predicts the view's per-tile costs, next to
+    the probe-sum estimate it corrects: rank correlation with the true tile
+    totals (recorded by the renderer) and RMSE on the log2(1 + total) / 32
+    scale the model is trained on."""
+    import numpy as np
+    import torch
+    nt = ((v.m + tile - 1) // tile) * ((v.n + tile - 1) // tile)
+    probe = torch.empty(nt * 64, dtype=torch.int32, device="cuda")
+    mb.mb_probe(v.window, v.m, v.n, v.iter_max, v.r2, probe, tile=tile, stream=stream)
+    feat = torch.empty((nt, 70), dtype=torch.float32, device="cuda")
+    mb.mb_tile_features(probe, v.window, v.m, v.n, v.iter_max, tile, feat, stream=stream)
+    y = torch.empty(nt, dtype=torch.float32, device="cuda")
+    mb.mb_mlp_forward(params, feat, nt, y, stream=stream)
+    tot = torch.zeros(nt, dtype=torch.int64, device="cuda")
+    out = torch.empty(v.m * v.n, dtype=torch.int32, device="cuda")
+    mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, out, sched="fcfs_tiles", tile=tile, tile_totals=tot,
+                 stream=stream)
+    tgt = torch.empty(nt, dtype=torch.float32, device="cuda")
+    mb.mb_tile_targets(tot, nt, tgt, stream=stream)
+    torch.cuda.synchronize()
+    t = tgt.cpu().numpy().astype(np.float64)
+    net = y.cpu().numpy().astype(np.float64)
+    ps = feat[:, 68].cpu().numpy().astype(np.float64)
+    return {"tiles": nt, "tile": tile,
+            "spearman": {"network": spearman(net, t), "probe_sum": spearman(ps, t)},
+            "rmse_log2_cost_over_32": {"network": float(np.sqrt(np.mean((net - t) ** 2))),
+                                       "probe_sum": float(np.sqrt(np.mean((ps - t) ** 2)))}}
+
+
 def cycle_variant(mb, v, ref, stream, args):
     """Time to the same binary64 image with exact cycle detection (mb_opts.cycle_check)
     against the same launch without it.  Reported as time only: the detected
@@ -496,6 +534,8 @@ def run_ours(args):
     }
     if learned:
         line["model"] = {"train_s": train_s, "probe_iterations": probe_iters}
+        if not args.no_compare:
+            line["model"]["quality"] = model_quality(mb, v, params, args.tile, stream)
 
     if not args.no_e2e:
         e2e = []
@@ -670,6 +710,8 @@ def run_ours(args):
         for k in zc:
             zc[k]["giter_s"] = zi / (zc[k]["ms"] * 1e-3) / 1e9
         line["zoom16384"] = {"iterations": zi, "variants": zc}
+        if params is not None:
+            line["zoom16384"]["model_quality"] = model_quality(mb, z, params, 64, None)
         if not args.no_precision:   # the reduced-precision variants on the deep zoom (pixel spacing 6e-10)
             zl = torch.empty_like(zo)
             lowp = {}

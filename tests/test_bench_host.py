@@ -48,3 +48,11 @@ def test_roofline_dram_context(monkeypatch):
     r = bench.roofline_entry(1000, 500.0, 1e12, 2.5e8)   # 250 MB in 0.5 s = 0.5 GB/s
     assert abs(r["dram_gbs"] - 0.5) < 1e-12 and abs(r["dram_frac_of_measured_hbm"] - 1e-4) < 1e-15
     assert bench.roofline_entry(1000, 500.0, 1e12, None)["dram_gbs"] is None
+
+
+def test_spearman():
+    import numpy as np
+    a = np.array([1.0, 2.0, 3.0, 4.0])
+    assert abs(bench.spearman(a, a * 10) - 1.0) < 1e-12
+    assert abs(bench.spearman(a, -a) + 1.0) < 1e-12
+    assert abs(bench.spearman(a, np.array([2.0, 1.0, 4.0, 3.0])) - 0.6) < 1e-12
