@@ -453,7 +453,7 @@ def run_ours(args):
     params, train_s = None, None
     if learned:
         t = time.perf_counter()
-        params, _ = tilemodel.default_model(stream=stream)
+        params, _ = tilemodel.default_model(tile=args.tile, stream=stream)
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t
 
@@ -684,7 +684,8 @@ def run_ours(args):
     if args.zoom:
         z = wl.ZOOM_3
         zo = torch.empty(z.m * z.n, dtype=torch.int32, device=dev)
-        runs = [("learned64", lambda: mb.mb_render_learned(z.window, z.m, z.n, z.iter_max, z.r2, zo, params, tile=64,
+        zparams = tilemodel.default_model(tile=64)[0] if params is not None else None
+        runs = [("learned64", lambda: mb.mb_render_learned(z.window, z.m, z.n, z.iter_max, z.r2, zo, zparams, tile=64,
                                                           block=args.block, unroll=args.unroll)),
                 ("probe_sum64", lambda: mb.mb_render_learned(z.window, z.m, z.n, z.iter_max, z.r2, zo, None, tile=64,
                                                             block=args.block, unroll=args.unroll)),
@@ -710,8 +711,8 @@ def run_ours(args):
         for k in zc:
             zc[k]["giter_s"] = zi / (zc[k]["ms"] * 1e-3) / 1e9
         line["zoom16384"] = {"iterations": zi, "variants": zc}
-        if params is not None:
-            line["zoom16384"]["model_quality"] = model_quality(mb, z, params, 64, None)
+        if zparams is not None:
+            line["zoom16384"]["model_quality"] = model_quality(mb, z, zparams, 64, None)
         if not args.no_precision:   # the reduced-precision variants on the deep zoom (pixel spacing 6e-10)
             zl = torch.empty_like(zo)
             lowp = {}

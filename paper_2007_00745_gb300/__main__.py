@@ -64,7 +64,7 @@ def main(argv=None):
             print("the learned order renders binary64 without cycle detection", file=sys.stderr)
             return 2
         from paper_2007_00745_gb300 import tilemodel
-        params, _ = tilemodel.default_model()
+        params, _ = tilemodel.default_model(tile=args.tile or 32)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     if params is not None:

@@ -54,9 +54,10 @@ def train(X, y, epochs=40, batch=256, lr=2e-3, seed=wl.SEED + 6, stream=None):
     return params, loss
 
 
-def default_model(train_views=32, side=1024, tile=64, epochs=40, stream=None, cache=True):
+def default_model(train_views=64, side=1024, tile=32, epochs=60, stream=None, cache=True):
     """The trained model used by the benchmark: trained on seeded zoom views
-    (training_zoom_views), cached under _build/ keyed by its recipe."""
+    (training_zoom_views) at the tile size it will order (its probe-sum feature
+    scales with the tile area), cached under _build/ keyed by its recipe."""
     import torch
     recipe = {"views": train_views, "side": side, "tile": tile, "epochs": epochs, "seed": wl.SEED,
               "lib": mb.mb_version(), "features": "probe-sum-residual-v3"}

@@ -56,8 +56,9 @@ def test_headline_configuration(orc, params):
     assert np.array_equal(got, orc.render_pixels(v.window, v.m, v.n, v.iter_max, v.r2, idx))
 
 
-def test_deep_zoom_configuration(orc, params):
+def test_deep_zoom_configuration(orc):
     z = wl.ZOOM_3
+    params = tilemodel.default_model(tile=64)[0]
     out = torch.full((z.m * z.n,), -1, dtype=torch.int32, device="cuda")
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     mb.mb_render_learned(z.window, z.m, z.n, z.iter_max, z.r2, out, params, tile=64, block=512, unroll=8, status=st)
