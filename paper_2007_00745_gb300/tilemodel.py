@@ -54,12 +54,12 @@ def train(X, y, epochs=40, batch=256, lr=2e-3, seed=wl.SEED + 6, stream=None):
     return params, loss
 
 
-def default_model(train_views=64, side=1024, tile=32, epochs=60, stream=None, cache=True):
+def default_model(train_views=64, side=1024, tile=32, epochs=200, lr=1e-3, stream=None, cache=True):
     """The trained model used by the benchmark: trained on seeded zoom views
     (training_zoom_views) at the tile size it will order (its probe-sum feature
     scales with the tile area), cached under _build/ keyed by its recipe."""
     import torch
-    recipe = {"views": train_views, "side": side, "tile": tile, "epochs": epochs, "seed": wl.SEED,
+    recipe = {"views": train_views, "side": side, "tile": tile, "epochs": epochs, "lr": lr, "seed": wl.SEED,
               "lib": mb.mb_version(), "features": "probe-sum-residual-v3"}
     key = hashlib.sha1(json.dumps(recipe, sort_keys=True).encode()).hexdigest()[:12]
     path = os.path.join(CACHE_DIR, "tile_model_%s.bin" % key)
@@ -71,7 +71,7 @@ def default_model(train_views=64, side=1024, tile=32, epochs=60, stream=None, ca
         except mb.MBError:
             pass   # unreadable or foreign file: train afresh
     X, y = build_training_set(wl.training_zoom_views(train_views, side), tile, stream=stream)
-    params, loss = train(X, y, epochs=epochs, stream=stream)
+    params, loss = train(X, y, epochs=epochs, lr=lr, stream=stream)
     if cache:
         os.makedirs(CACHE_DIR, exist_ok=True)
         torch.cuda.synchronize()
