@@ -151,7 +151,12 @@ const char* mb_strerror(int code);
  *   m, n     rows and columns, each in [1, 2^20]; fewer than 2^32 - 1 tiles
  *   iter_max iteration budget per pixel (0 allowed: every count is 0)
  *   escape_r2  squared escape radius R^2, finite and > 0
- *   out      device, m*n uint32, written in full
+ *   out      m*n uint32, written in full, in memory the current device can write: its own device
+ *            memory, managed memory, pinned / registered host memory (the kernels then store
+ *            the counts straight into host memory -- over NVLink-C2C on GB300 -- with no copy
+ *            step), or ordinary host memory where the device reports pageable memory access;
+ *            anything else is MB_EINVAL.  The same holds for mb_render_learned and for the
+ *            `out` of each mb_view.
  *   opt      host, may be NULL (all defaults); opt->precision selects binary64 (default,
  *            the paper's method, bit-exact) or a reduced-precision variant (mb_precision)
  * Errors: MB_EINVAL for bad arguments; MB_ENOMEM / MB_ECUDA from the launch. */

@@ -77,6 +77,8 @@ static int batch_prepare(const mb_view* views, uint32_t count, const mb_opts* op
   for (uint32_t i = 0; i < count; ++i) {
     rc = check_view(&views[i].w, views[i].m, views[i].n, views[i].escape_r2, views[i].out);
     if (rc) return rc;
+    rc = check_device_access(views[i].out);
+    if (rc) return rc;
     uint64_t t = (uint64_t)((views[i].n + tile - 1) / tile) * ((views[i].m + tile - 1) / tile);
     tiles[i] = (uint32_t)t;
     total_tiles += t;

@@ -29,6 +29,10 @@ using RenderFn = void (*)(RenderParams);
 bool filter_ok(double r2);
 EscThr make_thr(double r2);
 int check_view(const mb_window* w, uint32_t m, uint32_t n, double r2, const void* out);
+// MB_OK when the kernels of the current device can write through p: device memory of this
+// device, managed memory, pinned / registered host memory mapped at the same address, or
+// ordinary host memory on a device with pageable memory access (e.g. over NVLink-C2C).
+int check_device_access(const void* p);
 // Options an entry point honours beyond the common ones (check_opts rejects the others when set).
 enum OptAllow : unsigned { ALLOW_PRECISION = 1u, ALLOW_CYCLE = 2u };
 int check_opts(const mb_opts* o, uint32_t* log2_tile, unsigned allow = 0u);

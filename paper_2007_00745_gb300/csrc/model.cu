@@ -635,6 +635,8 @@ extern "C" int mb_render_learned(const mb_window* w, uint32_t m, uint32_t n, uin
                                  uint32_t* out, const float* params, const mb_opts* opt) {
   int rc = check_view(w, m, n, escape_r2, out);
   if (rc) return rc;
+  rc = check_device_access(out);
+  if (rc) return rc;
   uint32_t log2_tile = 0;
   rc = check_opts(opt, &log2_tile);
   if (rc) return rc;

@@ -48,6 +48,30 @@ int check_view(const mb_window* w, uint32_t m, uint32_t n, double r2, const void
   return MB_OK;
 }
 
+int check_device_access(const void* p) {
+  if (!p) return MB_EINVAL;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return MB_EINVAL;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MB_ECUDA;
+  switch (a.type) {
+    case cudaMemoryTypeDevice:
+      return a.device == dev ? MB_OK : MB_EINVAL;
+    case cudaMemoryTypeManaged:
+      return MB_OK;
+    case cudaMemoryTypeHost:  // pinned or registered: usable when the device sees it at the same address
+      return a.devicePointer == p ? MB_OK : MB_EINVAL;
+    default: {                // ordinary host memory: only where the device can access pageable memory
+      int pageable = 0;
+      if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) return MB_ECUDA;
+      return pageable ? MB_OK : MB_EINVAL;
+    }
+  }
+}
+
 int check_opts(const mb_opts* o, uint32_t* log2_tile, unsigned allow) {
   uint32_t tile = o && o->tile ? o->tile : DEFAULT_TILE;
   if (tile < 8 || tile > 256 || (tile & (tile - 1))) return MB_EINVAL;
@@ -176,6 +200,8 @@ extern "C" size_t mb_render_workspace_size(uint32_t m, uint32_t n, const mb_opts
 extern "C" int mb_render(const mb_window* w, uint32_t m, uint32_t n, uint32_t iter_max, double escape_r2,
                          uint32_t* out, const mb_opts* opt) {
   int rc = check_view(w, m, n, escape_r2, out);
+  if (rc) return rc;
+  rc = check_device_access(out);
   if (rc) return rc;
   uint32_t log2_tile = 0;
   rc = check_opts(opt, &log2_tile, ALLOW_PRECISION | ALLOW_CYCLE);
