@@ -82,6 +82,10 @@ def test_rejections_and_timeouts():
     assert e.value.code == mb.MB_ENOMEM
     heavy = wl.View((-0.3, 0.1, -0.3, 0.3), 256, 256, 2000000)      # interior: ~1.3e11 iterations
     a = srv.submit(heavy)
+    deadline = time.time() + 30   # admission runs on the server's worker thread: wait for it
+    while srv.counters()["admitted"] < 1 and time.time() < deadline:
+        time.sleep(0.001)
+    assert srv.counters()["admitted"] == 1
     b = srv.submit(heavy)   # waits for memory
     c = srv.submit(heavy)
     with pytest.raises(mb.MBError) as e:
@@ -109,6 +113,9 @@ def test_shutdown_cancels_queued_and_finishes_admitted():
     ts = [threading.Thread(target=waiter, args=(r,)) for r in (a, b)]
     for t in ts:
         t.start()
+    deadline = time.time() + 30   # let the worker admit a (b cannot fit beside it) before shutting down
+    while srv.counters()["admitted"] < 1 and time.time() < deadline:
+        time.sleep(0.001)
     time.sleep(0.05)
     srv.destroy()
     for t in ts:
