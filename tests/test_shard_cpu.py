@@ -64,3 +64,55 @@ def test_bad_arguments():
         shard.shard_tiles(10, 2, 2)
     with pytest.raises(ValueError):
         shard.shard_items([], 0, 0)
+
+
+def _fake_render(window, m, n, iter_max, r2, out, items, tile):
+    """Stand-in for the GPU render in this CPU test: writes the oracle's counts
+    of the listed tiles only (test infrastructure)."""
+    import numpy as np
+    import oracle
+    full = oracle.render(window, m, n, iter_max, r2).astype(np.int32)
+    img = out.view(m, n)
+    tiles_x = -(-n // tile)
+    for t, packed in items.tolist():
+        row0, rows = packed & 0xFFFF, (packed >> 16) & 0xFFFF
+        ty, tx = divmod(t, tiles_x)
+        r0, c0 = ty * tile + row0, tx * tile
+        r1, c1 = min(r0 + rows, m), min(c0 + tile, n)
+        img[r0:r1, c0:c1] = torch.from_numpy(full[r0:r1, c0:c1])
+
+
+def _sharded_worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    img = shard.render_sharded((-2.0, 1.0, -1.0, 1.0), 70, 101, 400, 4.0, tile=16, render=_fake_render)
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, None if img is None else img.numpy().copy()))
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_render_assembles_the_image(world):
+    """Ranks render disjoint tile shards of a ragged 70 x 101 view; the
+    sum-reduce on rank 0 is exactly the oracle's full image."""
+    import numpy as np
+    import oracle
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sharded_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=180) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    want = oracle.render((-2.0, 1.0, -1.0, 1.0), 70, 101, 400, 4.0)
+    assert np.array_equal(res[0].view(np.uint32).reshape(70, 101), want)
+    assert all(res[r] is None for r in range(1, world))
+
+
+def test_tile_items_cover_whole_tiles():
+    items = shard.tile_items([3, 0, 7], 32)
+    assert items.tolist() == [[3, 32 << 16], [0, 32 << 16], [7, 32 << 16]]
