@@ -33,3 +33,21 @@ def test_host_only_calls_work_without_gpu():
     assert mb.mb_version().startswith("mb ")
     assert mb.mb_strerror(1) == "invalid argument"
     assert mb.mb_strerror(99) == "unknown error"
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without libmb.so the first call raises ImportError: no CPU fallback."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = os.path.join(ROOT, "paper_2007_00745_gb300")
+    dst = tmp_path / "paper_2007_00745_gb300"
+    dst.mkdir()
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            shutil.copy(os.path.join(pkg, f), dst / f)
+    code = ("import sys; sys.path.insert(0, %r); import paper_2007_00745_gb300 as mb; "
+            "mb.mb_render((-2.0, 1.0, -1.0, 1.0), 4, 4, 10, 4.0, 0)") % str(tmp_path)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "libmb.so not built" in r.stderr
