@@ -128,9 +128,9 @@ typedef struct {
                                 only; a measured baseline), 0 = exactly on the integer pipes (default) */
   void* ev_start;            /* cudaEvent_t, optional: recorded on the stream right before the main render kernel */
   void* ev_stop;             /* cudaEvent_t, optional: recorded right after it (to time that kernel alone) */
-  uint32_t precision;        /* mb_precision; 0 = MB_PREC_FP64.  Other values are accepted by mb_render only
-                                (any scheduler; not with fp64_products); every other entry point returns
-                                MB_EINVAL for them */
+  uint32_t precision;        /* mb_precision; 0 = MB_PREC_FP64.  Other values are accepted by mb_render (any
+                                scheduler; not with fp64_products), mb_render_batch, mb_batch_plan_create and
+                                mb_serve_create; every other entry point returns MB_EINVAL for them */
   uint32_t cycle_check;      /* 1 = stop a pixel as soon as its binary64 state (zr, zi) at the start of a block of
                                 steps equals, bit for bit, its state at an earlier block start (kept at blocks
                                 1, 2, 4, 8, ...): the orbit is then periodic and never escapes, so the count is

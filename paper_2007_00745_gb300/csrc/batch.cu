@@ -68,7 +68,7 @@ struct BatchLayout {
 static int batch_prepare(const mb_view* views, uint32_t count, const mb_opts* opt, mb_batch_plan* P, bool graph) {
   if (!views || count == 0 || count > 65535) return MB_EINVAL;
   uint32_t log2_tile = 0;
-  int rc = check_opts(opt, &log2_tile, ALLOW_CYCLE);
+  int rc = check_opts(opt, &log2_tile, ALLOW_CYCLE | ALLOW_PRECISION);
   if (rc) return rc;
   const uint32_t tile = 1u << log2_tile;
   bool filt = true;
@@ -151,8 +151,10 @@ static int batch_prepare(const mb_view* views, uint32_t count, const mb_opts* op
   batch_items_kernel<<<ib, 256>>>((const uint32_t*)(P->dmem + L.prefix), (const uint32_t*)(P->dmem + L.vorder),
                                   count, tile, P->items);
   if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return MB_ECUDA;
-  P->fn = opt && opt->cycle_check ? render_fn_cycle(KIND_BATCH, S_FCFS, filt, (int)P->unroll)
-                                  : render_fn(KIND_BATCH, S_FCFS, filt, (int)P->unroll);
+  const int prec = opt ? (int)opt->precision : PREC_F64;
+  P->fn = prec != PREC_F64              ? render_fn_lowp(KIND_BATCH, S_FCFS, prec, (int)P->unroll)
+          : opt && opt->cycle_check ? render_fn_cycle(KIND_BATCH, S_FCFS, filt, (int)P->unroll)
+                                    : render_fn(KIND_BATCH, S_FCFS, filt, (int)P->unroll);
   P->grid = opt && opt->grid ? opt->grid : default_grid(P->fn, P->block);
   (void)graph;
   return MB_OK;

@@ -38,7 +38,7 @@ enum OptAllow : unsigned { ALLOW_PRECISION = 1u, ALLOW_CYCLE = 2u };
 int check_opts(const mb_opts* o, uint32_t* log2_tile, unsigned allow = 0u);
 RenderFn render_fn(int kind, int sched, bool filt, int unroll);
 RenderFn render_fn_fp64(bool filt);
-// binary32 / double-float kernels (render_lowp.cu): KIND_ROWS, KIND_RASTER and KIND_LIST
+// binary32 / double-float kernels (render_lowp.cu): KIND_ROWS, KIND_RASTER, KIND_LIST and KIND_BATCH
 RenderFn render_fn_lowp(int kind, int sched, int prec, int unroll);
 // binary64 kernels with exact cycle detection (render_cycle.cu): KIND_ROWS, KIND_RASTER, KIND_LIST
 // and KIND_BATCH; unroll 16, else 8

@@ -1,5 +1,6 @@
 // render_lowp.cu -- kernel table of the reduced-precision renders (binary32 and
-// double-float lanes of escape_lowp.cuh under the same schedulers as binary64).
+// double-float lanes of escape_lowp.cuh under the same schedulers as binary64,
+// and over the batched item list of mb_render_batch and the server).
 #include "mb_internal.h"
 #include "render_kernels.cuh"
 
@@ -21,6 +22,7 @@ RenderFn render_fn_lowp(int kind, int sched, int prec, int unroll) {
   }
   if (kind == KIND_RASTER) return pick_prec<KIND_RASTER, S_FCFS>(prec, unroll);
   if (kind == KIND_LIST) return pick_prec<KIND_LIST, S_FCFS>(prec, unroll);
+  if (kind == KIND_BATCH) return pick_prec<KIND_BATCH, S_FCFS>(prec, unroll);
   return nullptr;
 }
 

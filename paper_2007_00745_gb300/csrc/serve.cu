@@ -290,7 +290,7 @@ extern "C" int mb_serve_create(size_t mem_budget_bytes, uint32_t queue_limit, co
   if (!o.tile) o.tile = 32;
   if (!o.block) o.block = 512;
   if (!o.unroll) o.unroll = 8;
-  int rc = check_opts(&o, &log2_tile, ALLOW_CYCLE);
+  int rc = check_opts(&o, &log2_tile, ALLOW_CYCLE | ALLOW_PRECISION);
   if (rc) return rc;
   mb_server* S = new mb_server();
   S->budget = mem_budget_bytes;
@@ -299,10 +299,14 @@ extern "C" int mb_serve_create(size_t mem_budget_bytes, uint32_t queue_limit, co
   S->block = o.block;
   S->unroll = o.unroll;
   cudaGetDevice(&S->device);
-  S->fn_filt = o.cycle_check ? render_fn_cycle(KIND_BATCH, S_FCFS, true, (int)S->unroll)
-                             : render_fn(KIND_BATCH, S_FCFS, true, (int)S->unroll);
-  S->fn_exact = o.cycle_check ? render_fn_cycle(KIND_BATCH, S_FCFS, false, (int)S->unroll)
-                              : render_fn(KIND_BATCH, S_FCFS, false, (int)S->unroll);
+  if (o.precision != MB_PREC_FP64) {  // reduced-precision lanes take no escape filter
+    S->fn_filt = S->fn_exact = render_fn_lowp(KIND_BATCH, S_FCFS, (int)o.precision, (int)S->unroll);
+  } else {
+    S->fn_filt = o.cycle_check ? render_fn_cycle(KIND_BATCH, S_FCFS, true, (int)S->unroll)
+                               : render_fn(KIND_BATCH, S_FCFS, true, (int)S->unroll);
+    S->fn_exact = o.cycle_check ? render_fn_cycle(KIND_BATCH, S_FCFS, false, (int)S->unroll)
+                                : render_fn(KIND_BATCH, S_FCFS, false, (int)S->unroll);
+  }
   S->grid = o.grid ? o.grid : default_grid(S->fn_filt, S->block);
   S->round_tiles = o.round_tiles ? o.round_tiles : 16 * S->grid;
   cudaMemPoolProps props;

@@ -1,5 +1,6 @@
 """Parity of the reduced-precision renders (binary32, double-float) with their
-CPU oracle, through the C ABI.
+CPU oracle, through the C ABI: mb_render, batches (one-shot and graph) and the
+server.
 
 Each variant is defined by its exact operation sequence (include/mb.h,
 mb_precision), so the GPU counts must equal the oracle's bit for bit
@@ -101,9 +102,7 @@ def test_invalid_precision_requests_are_rejected():
         with pytest.raises(mb.MBError) as e:
             mb.mb_render(w, m, n, 100, 4.0, out, **kw)
         assert e.value.code == 1
-    with pytest.raises(mb.MBError):   # only mb_render honours a reduced precision
-        mb.mb_render_batch([(w, m, n, 100, 4.0)], [out], precision="dfloat")
-    with pytest.raises(mb.MBError):
+    with pytest.raises(mb.MBError):   # the no-alloc and learned paths are binary64 only
         mb.mb_render_noalloc(w, m, n, 100, 4.0, out, precision="fp32")
     with pytest.raises(mb.MBError):
         mb.mb_render_learned(w, m, n, 100, 4.0, out, None, precision="fp32")
@@ -144,3 +143,37 @@ def test_accuracy_against_binary64_on_the_gpu():
     df = float((outs["dfloat"] != outs["fp64"]).float().mean())
     print("mismatch vs binary64: fp32 %.5f, dfloat %.6f" % (f32, df))
     assert df * 10 < f32 and df < 1e-3
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_batch_and_plan(orc, precision):
+    views = wl.batch_views(count=9, seed=wl.SEED + 321, side_range=(1, 150), iter_range=(1, 3000))
+    for graph in (False, True):
+        outs = [torch.full((v.m * v.n,), -1, dtype=torch.int32, device="cuda") for v in views]
+        if graph:
+            plan = mb.BatchPlan(views, outs, tile=16, block=256, unroll=16, precision=precision)
+            plan.launch()
+            plan.launch()
+            plan.destroy()
+        else:
+            mb.mb_render_batch(views, outs, tile=32, precision=precision)
+        torch.cuda.synchronize()
+        for v, o in zip(views, outs):
+            got = o.cpu().numpy().view(np.uint32).reshape(v.m, v.n)
+            assert np.array_equal(got, orc.render_lowp(v.window, v.m, v.n, v.iter_max, v.r2, precision)), v
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_server(orc, precision):
+    views = wl.batch_views(count=8, seed=wl.SEED + 654, side_range=(8, 200), iter_range=(50, 4000))
+    srv = mb.Server(budget_bytes=1 << 28, precision=precision)
+    ids = [srv.submit(v) for v in views]
+    for rid, v in zip(ids, views):
+        rc, _ = srv.wait(rid, 120000)
+        assert rc == 0, rc
+        t = torch.empty(v.m * v.n, dtype=torch.int32, device="cuda")
+        srv.read(rid, t)
+        srv.release(rid)
+        got = t.cpu().numpy().view(np.uint32).reshape(v.m, v.n)
+        assert np.array_equal(got, orc.render_lowp(v.window, v.m, v.n, v.iter_max, v.r2, precision))
+    srv.destroy()
