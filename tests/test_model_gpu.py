@@ -115,6 +115,22 @@ def test_order_split_parity(ntiles, tile, grid, split):
     assert gl == om.order_and_split(y, tile, grid, split)
 
 
+def test_order_split_reports_a_too_small_capacity():
+    """An item list that does not fit the caller's capacity is not written:
+    n_items is 0 and status bit 2 is set (the learned render sizes it itself)."""
+    ntiles, tile, grid = 500, 64, 152
+    y = wl.random_costs(ntiles, seed=77)
+    need = len(om.order_and_split(y, tile, grid, 4))
+    cap = need - 1
+    items = torch.full((cap, 2), -1, dtype=torch.int32, device="cuda")
+    nit = torch.full((1,), 12345, dtype=torch.int32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    mb.mb_order_split(torch.from_numpy(y).cuda(), ntiles, tile, grid, items, cap, nit, st)
+    torch.cuda.synchronize()
+    assert int(nit.item()) == 0 and int(st.item()) & 2
+    assert (items.cpu() == -1).all()
+
+
 @pytest.mark.parametrize("fill", [float("nan"), -0.5, 0.0, float("inf")])
 def test_order_split_unusable_predictions(fill):
     """NaN / non-positive predictions give plain FCFS (raster order, no splits);
