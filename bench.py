@@ -43,7 +43,7 @@ FP64_PIPE_OPS_PER_ITER = 3  # of which issued on the FP64 pipe: the 3 additions 
 # profiles/render_kernel_list_8192x8192_it1000.md (dram read + write per launch
 # / pixels; traffic does not depend on iterMax, so it scales by pixel count);
 # used only while the kernel sources still hash to src_sha1, else null.
-NCU_RENDER = {"src_sha1": "ce1b8380bdba30f75732c9c25ae442165d11b382", "dram_bytes_per_pixel": 3.86}
+NCU_RENDER = {"src_sha1": "fe7236dd453478a4b67669e03d573d6aba74c31f", "dram_bytes_per_pixel": 3.85}
 KERNEL_SOURCES = ("escape_core.cuh", "escape_lowp.cuh", "render_kernels.cuh")
 
 

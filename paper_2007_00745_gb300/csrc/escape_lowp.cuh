@@ -20,10 +20,10 @@
 // parts; the escape test compares (h, l) pairs lexicographically.
 //
 // Neither variant needs the exactness machinery of the binary64 step.  The
-// iteration budget is applied once per block of steps (see resolve()): inside a
-// block a lane counts every non-escaping iteration even past iterMax; since the
-// count only grows while the orbit has not escaped, min(count, iterMax) is the
-// count the bounded loop would give.
+// binary32 lanes apply the iteration budget once per block of steps (see
+// resolve()): the count only grows while the orbit has not escaped, so adding
+// the block's iterations saturated at iterMax gives the count the bounded loop
+// would give.  The double-float lanes check the budget every iteration.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -101,8 +101,10 @@ __device__ __forceinline__ void step(LaneF32& L, double, EscThr) {
   }
 }
 
-// Settle a block: count it whole, or replay it to the escape; then apply the
-// budget (a lane that reached iterMax is done, with count iterMax).
+// Settle a block: count it whole, or replay it to the escape, never past the
+// budget (a lane that reaches iterMax is done, with count iterMax).  A live
+// lane has cnt < lim, and no sum below can exceed lim, so nothing wraps even
+// for iterMax near 2^32.
 template <int STEPS>
 __device__ __forceinline__ void resolve(LaneF32& L, double) {
   if (L.live) {
@@ -113,16 +115,15 @@ __device__ __forceinline__ void resolve(LaneF32& L, double) {
         bool e;
         f32_iter(zr, zi, L.cr, L.ci, L.r2, e);
         if (e) break;
-        ++c;
+        if (++c == L.lim) break;
       }
       L.cnt = c;
       L.live = false;
-    } else {
-      L.cnt += STEPS * F32_ITERS;
-    }
-    if (L.cnt >= L.lim) {
+    } else if (L.lim - L.cnt <= (uint32_t)(STEPS * F32_ITERS)) {
       L.cnt = L.lim;
       L.live = false;
+    } else {
+      L.cnt += STEPS * F32_ITERS;
     }
   }
 }
@@ -212,7 +213,7 @@ __device__ __forceinline__ void step(LaneF2& L, double, EscThr) {
   F2 zi2 = f2_mul(L.zi, L.zi);
   F2 s = f2_add(zr2, zi2);
   bool esc = s.h > L.r2.h || (s.h == L.r2.h && s.l > L.r2.l);
-  L.live = L.live && !esc;
+  L.live = L.live && !esc && L.cnt < L.lim;  // the budget each iteration: the count never passes iterMax
   L.cnt += L.live ? 1u : 0u;
   F2 twice_zr;
   twice_zr.h = __fadd_rn(L.zr.h, L.zr.h);
