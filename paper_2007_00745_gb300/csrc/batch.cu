@@ -266,13 +266,15 @@ static uint64_t fnv1a(const void* p, size_t n, uint64_t h) {
 }
 
 // key of a batch: its views (not their output pointers) and the sample stride
-static uint64_t batch_key(const mb_view* views, uint32_t count, uint32_t stride) {
+static uint64_t batch_key(const mb_view* views, uint32_t count, uint32_t stride, const mb_opts& base) {
   uint64_t h = 1469598103934665603ull;
   for (uint32_t i = 0; i < count; ++i) {
     h = fnv1a(&views[i].w, sizeof(mb_window), h);
     h = fnv1a(&views[i].m, 12, h);
     h = fnv1a(&views[i].escape_r2, 8, h);
   }
+  h = fnv1a(&base.precision, 4, h);    // the arithmetic changes the best launch shape
+  h = fnv1a(&base.cycle_check, 4, h);
   return fnv1a(&stride, 4, h);
 }
 
@@ -317,7 +319,7 @@ extern "C" int mb_batch_autotune(const mb_view* views, uint32_t count, const mb_
   std::memset(&b, 0, sizeof b);
   if (base) b = *base;
   b.grid = 0;
-  uint64_t key = batch_key(views, count, sample_stride);
+  uint64_t key = batch_key(views, count, sample_stride, b);
   float ms = 0.0f;
   if (cache_lookup(cache_path, key, &b, &ms)) {
     *best = b;
@@ -332,9 +334,13 @@ extern "C" int mb_batch_autotune(const mb_view* views, uint32_t count, const mb_
   float best_t = 1e30f;
   mb_opts winner = b;
   cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  int rc = MB_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess) return MB_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return MB_ECUDA;
+  }
+  int first_error = MB_OK;  // a candidate that fails (e.g. out of memory) is skipped
+  bool any = false;
   for (uint32_t t : tiles)
     for (uint32_t bl : blocks)
       for (uint32_t u : unrolls) {
@@ -344,8 +350,7 @@ extern "C" int mb_batch_autotune(const mb_view* views, uint32_t count, const mb_
         o.unroll = u;
         o.trace = nullptr;
         mb_batch_plan* P = nullptr;
-        rc = mb_batch_plan_create(sample.data(), (uint32_t)sample.size(), &o, &P);
-        if (rc) break;
+        int rc = mb_batch_plan_create(sample.data(), (uint32_t)sample.size(), &o, &P);
         float tm = 1e30f;
         for (int rep = 0; rep < 2 && rc == MB_OK; ++rep) {
           cudaEventRecord(e0, nullptr);
@@ -356,8 +361,12 @@ extern "C" int mb_batch_autotune(const mb_view* views, uint32_t count, const mb_
           cudaEventElapsedTime(&x, e0, e1);
           if (rep > 0) tm = x;  // first launch warms up
         }
-        mb_batch_plan_destroy(P);
-        if (rc) break;
+        if (P) mb_batch_plan_destroy(P);
+        if (rc) {
+          if (first_error == MB_OK) first_error = rc;
+          continue;
+        }
+        any = true;
         if (tm < best_t) {
           best_t = tm;
           winner = o;
@@ -365,7 +374,7 @@ extern "C" int mb_batch_autotune(const mb_view* views, uint32_t count, const mb_
       }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (rc) return rc;
+  if (!any) return first_error;
   *best = winner;
   if (best_ms) *best_ms = best_t;
   cache_store(cache_path, key, &winner, best_t);
