@@ -112,8 +112,25 @@ def mb_strerror(code):
 
 
 def mb_render(window, m, n, iter_max, escape_r2, out, **opts):
-    """Render an m x n image of escape counts into the device tensor `out`
-    (int32/uint32, m*n elements).  Keyword options mirror mb_opts."""
+    """Render an m x n image of escape counts into `out` (int32 tensor, m*n
+    elements, on the GPU or in pinned host memory), asynchronously on the
+    stream.  window = (xmin, xmax, ymin, ymax); escape_r2 = R^2.
+
+    Keyword options (mb_opts; 0 / None = default):
+      sched       "naive" | "alternating" | "fcfs_rows" | "fcfs_tiles" | "fcfs_items"
+      tile, block, grid, unroll   launch shape (power-of-two tile 8..256; block 32..512;
+                  grid = CTAs; unroll 4, 8 or 16)
+      items       int32 [K, 2] device tensor of (tile, row0 | rows << 16), for "fcfs_items"
+      precision   "fp64" (default, bit-exact binary64) | "fp32" | "dfloat"
+      cycle_check 1 = stop exactly periodic binary64 orbits early (identical counts)
+      status      int32 device tensor: error bits (1 bounded wait, 2 bad item, 4 deadline)
+      trace       int64 device tensor, 3 per CTA: (start_ns, end_ns, smid | items << 32)
+      tile_totals int64 device tensor: += per-tile sums of the counts
+      max_seconds per-launch time limit (default DEFAULT_MAX_SECONDS, 0 = none)
+      events      (start, stop) torch.cuda.Event pair recorded around the render kernel
+      workspace   caller-owned device temporaries (mb_render_workspace_size bytes)
+      stream      torch.cuda.Stream or raw handle (default: the current stream)
+    Raises MBError with the library's code on invalid arguments."""
     L = _L()
     w = L.mb_window(*map(float, window))
     o = _opts(**opts)
