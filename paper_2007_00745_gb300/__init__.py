@@ -199,6 +199,7 @@ def mb_selftest_products(a, b, sq, pr, ok, stream=None):
 
 
 def mb_device_info(block=0):
+    """(SM count, resident render CTAs per SM at `block` threads) of the current device."""
     L = _L()
     a, b = ctypes.c_uint32(), ctypes.c_uint32()
     _check(L.lib().mb_device_info(int(block), ctypes.byref(a), ctypes.byref(b)), "mb_device_info")
@@ -221,6 +222,7 @@ def mb_probe(window, m, n, iter_max, escape_r2, probe_out, image_out=None, **opt
 
 
 def mb_tile_features(probe, window, m, n, iter_max, tile, feat, stream=None):
+    """70 features per tile (float32 [tiles, 70]) from its probe counts."""
     L = _L()
     w = L.mb_window(*map(float, window))
     _check(L.lib().mb_tile_features(_ptr(probe), ctypes.byref(w), int(m), int(n), int(iter_max), int(tile),
@@ -228,36 +230,50 @@ def mb_tile_features(probe, window, m, n, iter_max, tile, feat, stream=None):
 
 
 def mb_tile_targets(totals, ntiles, y, stream=None):
+    """Training targets log2(1 + total) / 32 from per-tile totals (int64)."""
     _check(_L().lib().mb_tile_targets(_ptr(totals), int(ntiles), _ptr(y), _stream(stream)), "mb_tile_targets")
 
 
 def mb_mlp_forward(params, x, count, y, stream=None):
+    """Predicted log tile cost y[count] of the network for feature rows x[count, 70]."""
     _check(_L().lib().mb_mlp_forward(_ptr(params), _ptr(x), int(count), _ptr(y), _stream(stream)), "mb_mlp_forward")
 
 
 def mb_mlp_grad(params, x, idx, batch, target, grad, loss=None, stream=None):
+    """Gradient of the mean squared error over the rows idx[batch] into grad (and the loss)."""
     _check(_L().lib().mb_mlp_grad(_ptr(params), _ptr(x), _ptr(idx), int(batch), _ptr(target), _ptr(grad),
                                   _ptr(loss), _stream(stream)), "mb_mlp_grad")
 
 
 def mb_adam_step(params, grad, m, v, count, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """One Adam update of `count` parameters at step t (1-based), in place."""
     _check(_L().lib().mb_adam_step(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(count), int(t), float(lr),
                                    float(beta1), float(beta2), float(eps), _stream(stream)), "mb_adam_step")
 
 
 def mb_model_train(params, adam_m, adam_v, x, target, count, order, epochs, batch, lr=1e-3, epoch_loss=None,
                    stream=None):
+    """Trains in place on the GPU: `epochs` passes over `count` rows in the given
+    per-epoch orders (int32 [epochs, count]), mini-batches of `batch`, Adam at
+    learning rate lr; epoch_loss[epochs] receives the mean loss of each epoch."""
     _check(_L().lib().mb_model_train(_ptr(params), _ptr(adam_m), _ptr(adam_v), _ptr(x), _ptr(target), int(count),
                                      _ptr(order), int(epochs), int(batch), float(lr), _ptr(epoch_loss),
                                      _stream(stream)), "mb_model_train")
 
 
 def mb_order_split(cost_pred, ntiles, tile, grid, items, capacity, n_items, status=None, stream=None, split=4):
+    """Longest-first item list (with splits) from predicted costs; n_items = 0 and
+    status bit 2 when it does not fit `capacity`."""
     _check(_L().lib().mb_order_split(_ptr(cost_pred), int(ntiles), int(tile), int(grid), int(split), _ptr(items),
                                      int(capacity), _ptr(n_items), _ptr(status), _stream(stream)), "mb_order_split")
 
 
 def mb_render_learned(window, m, n, iter_max, escape_r2, out, params, **opts):
+    """The learned pipeline: probe (8 x 8 samples per tile, written into `out`), tile
+    features, predicted costs (`params`: the 8769 float32 parameters on the device, or
+    None for the probe-sum order), longest-first order with splits, then the FCFS
+    render of the remaining pixels.  Options as mb_render (tile >= 16; `split` is the
+    split divisor).  Binary64 only."""
     L = _L()
     w = L.mb_window(*map(float, window))
     o = _opts(**opts)
@@ -266,10 +282,12 @@ def mb_render_learned(window, m, n, iter_max, escape_r2, out, params, **opts):
 
 
 def mb_model_save(params, path):
+    """Writes the parameters to `path` (magic MBMLP701, count, float32 values)."""
     _check(_L().lib().mb_model_save(_ptr(params), str(path).encode()), "mb_model_save")
 
 
 def mb_model_load(path, params):
+    """Reads parameters written by mb_model_save; MBError on a bad or foreign file."""
     _check(_L().lib().mb_model_load(str(path).encode(), _ptr(params)), "mb_model_load")
 
 
