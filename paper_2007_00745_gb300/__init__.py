@@ -104,10 +104,12 @@ def _check(rc, where):
 
 
 def mb_version():
+    """Library version string."""
     return _L().lib().mb_version().decode()
 
 
 def mb_strerror(code):
+    """Name of a return code."""
     return _L().lib().mb_strerror(int(code)).decode()
 
 
@@ -153,6 +155,7 @@ def mb_render_noalloc(window, m, n, iter_max, escape_r2, out, **opts):
 
 
 def mb_render_workspace_size(m, n, **opts):
+    """Bytes of caller workspace mb_render needs for an m x n view."""
     L = _L()
     o = _opts(**opts)
     return int(L.lib().mb_render_workspace_size(int(m), int(n), ctypes.byref(o)))
