@@ -597,6 +597,9 @@ extern "C" int mb_probe(const mb_window* w, uint32_t m, uint32_t n, uint32_t ite
                         uint32_t* probe_out, uint32_t* image_out, const mb_opts* opt) {
   int rc = check_view(w, m, n, escape_r2, probe_out);
   if (rc) return rc;
+  rc = check_device_access(probe_out);
+  if (rc == MB_OK && image_out) rc = check_device_access(image_out);
+  if (rc) return rc;
   uint32_t log2_tile = 0;
   rc = check_opts(opt, &log2_tile);
   if (rc) return rc;
