@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-compare", action="store_true", help="skip the per-scheduler comparison")
     p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--batch-count", type=int, default=256,
+                   help="viewports in the batch (default 256; fewer for profiling runs)")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-precision", action="store_true", help="skip the binary32 / double-float variants")
     p.add_argument("--no-cycle", action="store_true", help="skip the exact-cycle-detection timing")
@@ -649,7 +651,7 @@ def run_ours(args):
         line["cycle_check"] = cycle_variant(mb, v, out, stream, args)
 
     if not args.no_batch:
-        views = wl.batch_views(256)
+        views = wl.batch_views(args.batch_count)
         outs = [torch.empty(q.m * q.n, dtype=torch.int32, device=dev) for q in views]
         cache = os.path.join(ROOT, "paper_2007_00745_gb300", "_build", "autotune_cache.txt")
         os.makedirs(os.path.dirname(cache), exist_ok=True)
@@ -673,7 +675,7 @@ def run_ours(args):
         info = plan.info()
         plan.destroy()
         bm = min(bms)
-        line["batch"] = {"workload": "256 viewports, sides U(256..4096), widths log-U(1e-9..1e-1), "
+        line["batch"] = {"workload": "%d viewports, sides U(256..4096), widths log-U(1e-9..1e-1), " % len(views) +
                                      "iterMax log-U(256..65536), one persistent launch, CUDA graph replay",
                          "giter_s": bi / (bm * 1e-3) / 1e9, "ms": bm, "iterations": bi, "items": info["items"],
                          "pixels": info["pixels"], "autotuned": best, "autotune_sample_ms": tune_ms}
