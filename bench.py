@@ -524,9 +524,12 @@ def run_ours(args):
         "metric": "Giter/s", "value": value, "unit": "Giter/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "%dx%d re[-2,1] im[-1.5,1.5] iterMax %d R2 4, %s FCFS (tile %d, block %d, unroll %d)"
-                               % (v.m, v.n, v.iter_max, args.sched, args.tile, args.block, args.unroll),
-                   "iterations_per_step": iters, "l2": "counts 268 MB per step > 129 MB L2 (compute-bound)",
+        "config": {"workload": "%dx%d re[-2,1] im[-1.5,1.5] iterMax %d R2 4, %s (tile %d, block %d, unroll %d)"
+                               % (v.m, v.n, v.iter_max, "learned FCFS" if learned else args.sched, args.tile,
+                                  args.block, args.unroll),
+                   "iterations_per_step": iters,
+                   "l2": "counts %.0f MB per step %s 129 MB L2 (compute-bound)"
+                         % (v.m * v.n * 4 / 1e6, ">" if v.m * v.n * 4 > 129e6 else "<="),
                    "parallelism": "replicas" if ws > 1 else "1 GPU", "bit_exact": "vs FP64 oracle (tests)"},
         "roofline": roofline_entry(render_iters, kernel_ms, peak, traffic),
         "pct_fp64_peak": 100.0 * value * 1e9 * ALG_OPS_PER_ITER / peak,
