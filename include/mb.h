@@ -283,8 +283,11 @@ typedef struct {
 
 typedef struct mb_server mb_server;
 
-/* opts: tile (default 32), block (512), unroll (8), grid, round_tiles; other fields ignored.
- * queue_limit 0 = 1024. */
+/* opts: tile (default 32), block (512), unroll (8), grid, round_tiles, precision and
+ * cycle_check (as for mb_render, applied to every request); other fields ignored.
+ * queue_limit 0 = 1024.  The budget is a charge, not a reservation: if the device
+ * cannot allocate an admitted request's memory (a budget above the free device
+ * memory), every pending request fails with MB_ECUDA and later calls return it. */
 int mb_serve_create(size_t mem_budget_bytes, uint32_t queue_limit, const mb_opts* opt, mb_server** s);
 /* MB_ENOMEM if the request alone exceeds the budget, MB_EBUSY if the queue is full. */
 int mb_serve_submit(mb_server* s, const mb_request* rq, uint64_t* id);
