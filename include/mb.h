@@ -140,10 +140,10 @@ typedef struct {
                                 return MB_EINVAL for it; 0 = off */
 } mb_opts;
 
-/* Library version string. */
+/* Library version string (not in the paper). */
 const char* mb_version(void);
 
-/* Human-readable name of a return code. */
+/* Human-readable name of a return code (not in the paper). */
 const char* mb_strerror(int code);
 
 /* Render one image (Eq. 2 for all i < m, j < n).
@@ -166,8 +166,8 @@ int mb_render(const mb_window* w, uint32_t m, uint32_t n, uint32_t iter_max, dou
 /* Largest m and n that mb_render_noalloc accepts. */
 #define MB_NOALLOC_MAX_SIDE 16384
 
-/* The paper has no counterpart to this entry point; it exists for callers that
- * must not allocate device memory.  It renders exactly what mb_render renders
+/* Not in the paper as an entry point (its counts are the Eq. 2 counts of
+ * mb_render): it exists for callers that must not allocate device memory.  It renders exactly what mb_render renders
  * (same arguments, same counts, same options except `workspace`, which must be
  * NULL, and `precision`, which must be MB_PREC_FP64), but calls no cudaMalloc / cudaMallocAsync / cudaFree: the temporary
  * memory it needs sits in one fixed array inside the library's device image
@@ -186,11 +186,13 @@ int mb_render_noalloc(const mb_window* w, uint32_t m, uint32_t n, uint32_t iter_
                       uint32_t* out, const mb_opts* opt);
 
 /* Bytes of temporary device memory mb_render needs for this size and options
- * (Cx/Cy arrays and work counters), so that a caller can pass opts->workspace. */
+ * (the Cx/Cy arrays of Sec. III-A and the work counters of the Sec. III-B
+ * scheduler), so that a caller can pass opts->workspace. */
 size_t mb_render_workspace_size(uint32_t m, uint32_t n, const mb_opts* opt);
 
 /* Sum of `count` uint32 values (device) into *total (device uint64, overwritten),
- * i.e. the number of z-updates of a rendered image. */
+ * i.e. the number of z-updates of a rendered image: the sum of its Eq. 2 counts,
+ * the work unit of every throughput figure (not an operation of the paper). */
 int mb_sum_counts(const uint32_t* counts, uint64_t count, uint64_t* total, void* stream);
 
 /* Statistics of one render launch (the per-worker accounting behind the paper's
@@ -222,6 +224,8 @@ typedef struct {
 int mb_last_stats(mb_run_stats* st);
 
 /* ---- batched mode: many viewports in one persistent launch ----
+ * Not in the paper: one first-come-first-served worker pool (Sec. III-B) over
+ * the tiles of many images at once; every image's counts are those of Eq. 2.
  * A view: window, size, iteration budget, R^2 and its own output buffer
  * (device, m*n uint32).  Each view is rendered exactly as mb_render would. */
 typedef struct {
@@ -255,7 +259,8 @@ int mb_batch_autotune(const mb_view* views, uint32_t count, const mb_opts* base,
                       const char* cache_path, mb_opts* best, float* best_ms);
 
 /* ---- serving: continuous batching under a device-memory budget ----
- * A request is one view; the server allocates its counts (m*n uint32) and Cx/Cy
+ * Not in the paper: requests share first-come-first-served rounds (Sec. III-B);
+ * every request's counts are those of Eq. 2.  A request is one view; the server allocates its counts (m*n uint32) and Cx/Cy
  * arrays on the device, charging align256(m*n*4) + align256((m+n)*8) bytes to
  * the budget until the request is released.  Requests that do not fit yet wait
  * in a FIFO of at most queue_limit entries.  A worker thread keeps four rounds
@@ -406,7 +411,8 @@ int mb_colorize(const uint32_t* counts, uint64_t count, uint32_t iter_max, uint8
 /* Writes a binary PPM (P6, maxval 255) of m rows x n columns from rgb (host). */
 int mb_write_ppm(const char* path, const uint8_t* rgb, uint32_t m, uint32_t n);
 
-/* FP64 issue-rate microbenchmark: runs independent chains of one binary64
+/* FP64 issue-rate microbenchmark (not in the paper; the measurement's
+ * denominator): runs independent chains of one binary64
  * operation (op: 0 = add, 1 = mul, 2 = fma) on every SM and returns the
  * measured rate in operations per second (a fused multiply-add counts as one
  * operation) and the elapsed kernel time.  Synchronous.  This rate is the
@@ -431,7 +437,8 @@ int mb_selftest_products(const double* a, const double* b, uint64_t n, double* s
  * context stays usable.  MB_EINVAL for NULL pointers or ctas outside [1, 1024]. */
 int mb_selftest_wait(uint32_t ctas, uint32_t* status, uint32_t* got, void* stream);
 
-/* Number of SMs and resident CTAs per SM the render kernel gets at `block` threads. */
+/* Number of SMs and resident CTAs per SM the render kernel gets at `block`
+ * threads: the worker count G of the Sec. III schedulers at the default grid. */
 int mb_device_info(uint32_t block, uint32_t* sms, uint32_t* ctas_per_sm);
 
 #ifdef __cplusplus
