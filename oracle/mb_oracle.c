@@ -187,6 +187,7 @@ uint32_t mbo_alternating_owner(uint32_t i, uint32_t workers) { return i % worker
  * g = tri((5k) mod 512), b = tri((3k) mod 512).  Integers only. */
 static unsigned tri(unsigned x) { return x < 256u ? x : 511u - x; }
 
+/* Sec. I colouring of every count with the palette above. */
 void mbo_colorize(const uint32_t* counts, uint64_t count, uint32_t iter_max, uint8_t* rgb) {
   for (uint64_t t = 0; t < count; t++) {
     uint32_t k = counts[t];
@@ -202,7 +203,8 @@ void mbo_colorize(const uint32_t* counts, uint64_t count, uint32_t iter_max, uin
   }
 }
 
-/* Host threads the OpenMP loops above use (the core count reported with the CPU baseline). */
+/* Host threads the OpenMP loops above use (the core count reported with the CPU
+ * baseline; not a step of the method). */
 int mbo_max_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

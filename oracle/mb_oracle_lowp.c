@@ -46,11 +46,14 @@
 #include <omp.h>
 #endif
 
+/* The binary64 pixel map (Cx / Cy of Sec. III-A), from mb_oracle.c. */
 double mbo_c_re(double xmin, double xmax, uint32_t n, uint32_t j);
 double mbo_c_im(double ymin, double ymax, uint32_t m, uint32_t i);
 
 /* ---- binary32 ------------------------------------------------------------- */
 
+/* Eq. 1-2 in binary32 (not in the paper, which computes in double precision):
+ * c and R^2 rounded once, then the binary64 operation order in binary32. */
 uint32_t mbo_escape_f32(double cr64, double ci64, uint32_t iter_max, double r2_64) {
   float cr = (float)cr64, ci = (float)ci64, r2 = (float)r2_64;
   float zr = 0.0f, zi = 0.0f;
@@ -92,13 +95,15 @@ void mbo_fast_two_sum(float a, float b, float* s, float* e) {
   *e = b - b_virtual;
 }
 
-/* Exact product a * b = p + e (the error term from one fused multiply-add). */
+/* Exact product a * b = p + e (the error term from one fused multiply-add; the
+ * two-product of the double-word algorithms of Joldes, Muller and Popescu). */
 void mbo_two_prod(float a, float b, float* p, float* e) {
   float prod = a * b;
   *p = prod;
   *e = fmaf(a, b, -prod);
 }
 
+/* A binary64 value as a double-float pair (the conversion described above). */
 mbo_df mbo_df_from_f64(double x) {
   mbo_df r;
   r.h = (float)x;
@@ -148,6 +153,9 @@ static mbo_df df_twice(mbo_df x) {
 
 static int df_greater(mbo_df a, mbo_df b) { return a.h > b.h || (a.h == b.h && a.l > b.l); }
 
+/* Eq. 1-2 in double-float arithmetic (not in the paper): the binary64
+ * operation order with the double-word sum and product above, 2*zr by doubling
+ * both parts, and the lexicographic escape test. */
 uint32_t mbo_escape_df(double cr64, double ci64, uint32_t iter_max, double r2_64) {
   mbo_df cr = mbo_df_from_f64(cr64), ci = mbo_df_from_f64(ci64), r2 = mbo_df_from_f64(r2_64);
   mbo_df zr = {0.0f, 0.0f}, zi = {0.0f, 0.0f};
@@ -164,7 +172,8 @@ uint32_t mbo_escape_df(double cr64, double ci64, uint32_t iter_max, double r2_64
   return k;
 }
 
-/* Flat wrappers of the double-float primitives (for the tests' exact checks). */
+/* Flat wrappers of the double-float primitives (test infrastructure: the
+ * pins check them against exact rationals and their published error bounds). */
 void mbo_df_add4(float xh, float xl, float yh, float yl, float* zh, float* zl) {
   mbo_df x = {xh, xl}, y = {yh, yl};
   mbo_df z = mbo_df_add(x, y);
@@ -181,8 +190,8 @@ void mbo_df_mul4(float xh, float xl, float yh, float yl, float* zh, float* zl) {
 
 /* ---- images ------------------------------------------------------------------ */
 
-/* Whole image in the given precision (1 = binary32, 2 = double-float), rows
- * [row0, row0 + nrows) only, out[(i - row0) * n + j]. */
+/* Eq. 2 over the image in the given precision (1 = binary32, 2 = double-float;
+ * not in the paper), rows [row0, row0 + nrows) only, out[(i - row0) * n + j]. */
 void mbo_render_rows_lowp(double xmin, double xmax, double ymin, double ymax, uint32_t m, uint32_t n,
                           uint32_t iter_max, double r2, int precision, uint32_t row0, uint32_t nrows,
                           uint32_t* out, int threads) {
