@@ -21,3 +21,18 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "Giter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert "256x256" in d["config"]["workload"] and "iterMax 500" in d["config"]["workload"]
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """Launched as the benchmark's N>1 command (torchrun, 2 ranks): rank 0 alone
+    times the oracle and prints the line; the other rank exits 0 without work."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", "29531", os.path.join(ROOT, "bench.py"),
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "1", "--size", "128",
+           "--iter-max", "200"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
