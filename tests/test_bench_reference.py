@@ -2,6 +2,7 @@
 JSON line with the contract's keys.  Runs on the CPU, on a small view."""
 import json
 import os
+import socket
 import subprocess
 import sys
 
@@ -26,8 +27,11 @@ def test_reference_arm_json_line():
 def test_reference_arm_under_torchrun_prints_once():
     """Launched as the benchmark's N>1 command (torchrun, 2 ranks): rank 0 alone
     times the oracle and prints the line; the other rank exits 0 without work."""
+    with socket.socket() as sk:          # a free port for the rendezvous
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
-           "--master-addr", "127.0.0.1", "--master-port", "29531", os.path.join(ROOT, "bench.py"),
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
            "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "1", "--size", "128",
            "--iter-max", "200"]
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=ROOT)
