@@ -166,22 +166,27 @@ int mb_render(const mb_window* w, uint32_t m, uint32_t n, uint32_t iter_max, dou
 /* Largest m and n that mb_render_noalloc accepts. */
 #define MB_NOALLOC_MAX_SIDE 16384
 
-/* Not in the paper as an entry point (its counts are the Eq. 2 counts of
- * mb_render): it exists for callers that must not allocate device memory.  It renders exactly what mb_render renders
- * (same arguments, same counts, same options except `workspace`, which must be
- * NULL, and `precision`, which must be MB_PREC_FP64), but calls no cudaMalloc / cudaMallocAsync / cudaFree: the temporary
- * memory it needs sits in one fixed array inside the library's device image
- * (262,656 bytes, resident on every GPU that loads the library until exit).
- * Typical callers: code running where the allocator may not be entered (host
- * callbacks, real-time loops), or processes whose device memory another
- * framework has reserved up front.
+/* Not in the paper: there is no counterpart of this entry point there.  It exists
+ * for callers that must not allocate device memory -- code running where the
+ * allocator may not be entered (host callbacks, real-time loops), or processes
+ * whose device memory another framework has reserved up front.  Its counts are
+ * those of mb_render for the same arguments, but it calls no cudaMalloc /
+ * cudaMallocAsync / cudaFree: the temporary memory it needs sits in one fixed
+ * array inside the library's device image (262,656 bytes, resident on every GPU
+ * that loads the library until exit).
  *   m, n   each in [1, MB_NOALLOC_MAX_SIDE]; larger sizes return MB_EINVAL.
- * All calls on a device share the array and it keeps the last call's contents;
- * every part a render reads is rewritten (the work counter zeroed) on the
- * stream before the render kernel runs.  Calls whose kernels overlap on the
- * GPU race on the array: issue them on one stream.  The first call on a device
- * looks up the array's address (cudaGetSymbolAddress); make it before any
- * stream capture starts. */
+ *   out    as mb_render (checked the same way before any launch).
+ *   opt    as mb_render: sched, tile, block, grid, unroll, items / n_items,
+ *          tile_totals, trace, status, max_seconds, ev_start / ev_stop and stream
+ *          are honoured.  Rejected with MB_EINVAL: workspace (the fixed array is
+ *          the workspace), precision other than MB_PREC_FP64, cycle_check and
+ *          fp64_products (their kernels come with mb_render only).
+ * Nothing is recorded for mb_last_stats.  All calls on a device share the
+ * array and it keeps the last call's contents; every part a render reads is
+ * rewritten (the work counter zeroed) on the stream before the render kernel
+ * runs.  Calls whose kernels overlap on the GPU race on the array: issue them
+ * on one stream.  The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress); make it before any stream capture starts. */
 int mb_render_noalloc(const mb_window* w, uint32_t m, uint32_t n, uint32_t iter_max, double escape_r2,
                       uint32_t* out, const mb_opts* opt);
 

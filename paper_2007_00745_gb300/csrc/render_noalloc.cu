@@ -79,10 +79,13 @@ extern "C" int mb_render_noalloc(const mb_window* w, uint32_t m, uint32_t n, uin
   int rc = check_view(w, m, n, escape_r2, out);
   if (rc) return rc;
   if (m > NOALLOC_MAX_SIDE || n > NOALLOC_MAX_SIDE) return MB_EINVAL;
-  uint32_t log2_tile = 0;
-  rc = check_opts(opt, &log2_tile);
+  rc = check_device_access(out);
   if (rc) return rc;
-  if (opt && opt->workspace) return MB_EINVAL;  // the fixed array is the workspace here
+  uint32_t log2_tile = 0;
+  rc = check_opts(opt, &log2_tile);  // rejects precision != binary64 and cycle_check
+  if (rc) return rc;
+  if (opt && opt->workspace) return MB_EINVAL;    // the fixed array is the workspace here
+  if (opt && opt->fp64_products) return MB_EINVAL;  // the all-FP64 baseline kernel comes with mb_render only
   const int sched = opt ? opt->sched : MB_SCHED_FCFS_TILES;
   const uint32_t block = opt && opt->block ? opt->block : DEFAULT_BLOCK;
   cudaStream_t st = opt ? (cudaStream_t)opt->stream : nullptr;
@@ -119,6 +122,7 @@ extern "C" int mb_render_noalloc(const mb_window* w, uint32_t m, uint32_t n, uin
   P.status = opt ? opt->status : nullptr;
   P.trace = opt ? opt->trace : nullptr;
   P.trace_len = opt && opt->trace ? opt->trace_len : 0;
+  P.deadline_ns = opt_deadline_ns(opt);
 
   int kind, s;
   switch (sched) {
@@ -135,5 +139,5 @@ extern "C" int mb_render_noalloc(const mb_window* w, uint32_t m, uint32_t n, uin
   if (map_blocks > 1024) map_blocks = 1024;
   pixel_map_single_kernel<<<map_blocks, 256, 0, st>>>(V, (ViewDesc*)(ws + NOALLOC_VIEW), P.counter);
   if (cudaGetLastError() != cudaSuccess) return MB_ECUDA;
-  return launch_render(fn, P, grid, block, st);
+  return launch_render_timed(fn, P, grid, block, st, opt);
 }
