@@ -1,10 +1,13 @@
-"""Write tests/golden/boundary_points.json: centres near the Mandelbrot boundary.
+"""Write paper_2007_00745_gb300/data/boundary_points.json: centres near the Mandelbrot boundary.
 
 Renders the 1024 x 1024 full view re[-2, 1] x im[-1.5, 1.5] at iterMax 65536
 with the CPU oracle only, keeps the pixels whose count is in [50, 65536) and
 stores a seeded subsample of their c values.  The batched and served
 workloads (and the tile-cost model's training windows) draw their centres
-from this list.  Run from the repository root:  python tests/golden/make_boundary_manifest.py
+from this list.  Run from the repository root:  python oracle/make_boundary_manifest.py
+
+Test infrastructure like the rest of oracle/: the package only reads the
+JSON file it writes (input data, no method arithmetic), never this script.
 """
 import json
 import os
@@ -12,7 +15,7 @@ import sys
 
 import numpy as np
 
-ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
 import oracle  # noqa: E402
@@ -30,7 +33,7 @@ def main():
     pts = [[float(cx[jj[k]]), float(cy[ii[k]])] for k in pick]
     out = {"window": WINDOW, "side": SIDE, "iter_max": ITER_MAX, "count_range": [50, ITER_MAX],
            "candidates": int(len(ii)), "seed": SEED, "points": pts}
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "boundary_points.json")
+    path = os.path.join(ROOT, "paper_2007_00745_gb300", "data", "boundary_points.json")
     with open(path, "w") as f:
         json.dump(out, f)
     print(path, len(pts), "of", len(ii))

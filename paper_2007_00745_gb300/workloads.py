@@ -3,14 +3,14 @@
 Inputs only: windows, sizes, iteration budgets and seeded samplers.  Nothing
 here evaluates the escape-time method; where a workload needs counts to pick
 its inputs (the batch viewports), those come from a manifest file written once
-by a committed script that calls the CPU oracle (tests/golden/).
+by a committed script that calls the CPU oracle (oracle/make_boundary_manifest.py)
+into this package's data/ folder.
 """
 import json
 import math
 import os
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-GOLDEN = os.path.join(ROOT, "tests", "golden")
+DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
 
 SEED = 200700745
 
@@ -95,8 +95,8 @@ def training_zoom_views(count, side, seed=SEED + 3, iter_max_range=(2048, 32768)
 def boundary_points():
     """Centres near the set's boundary: pixels of a 1024^2 full-view render
     (re[-2,1] im[-1.5,1.5], iterMax 65536) with count in [50, 65536), as
-    written by tests/golden/make_boundary_manifest.py."""
-    path = os.path.join(GOLDEN, "boundary_points.json")
+    written by oracle/make_boundary_manifest.py into data/."""
+    path = os.path.join(DATA, "boundary_points.json")
     with open(path) as f:
         d = json.load(f)
     return [tuple(p) for p in d["points"]]

@@ -58,6 +58,17 @@ def test_boundary_manifest():
     assert xs.min() >= -2.0 and xs.max() < 1.0 and ys.min() > -1.5 and ys.max() <= 1.5
 
 
+def test_boundary_manifest_counts_from_the_oracle(orc):
+    # the recipe of the package's data file: every centre is a pixel of the
+    # 1024^2 full view whose oracle count lies in [50, 65536)
+    pts = wl.boundary_points()
+    cx, cy = orc.pixel_map((-2.0, 1.0, -1.5, 1.5), 1024, 1024)
+    xs, ys = set(map(float, cx)), set(map(float, cy))
+    for x, y in pts[::8]:
+        assert x in xs and y in ys
+        assert 50 <= orc.escape(x, y, 65536) < 65536
+
+
 def test_batch_views_recipe():
     views = wl.batch_views(256)
     assert views == wl.batch_views(256)                    # seeded
