@@ -77,7 +77,9 @@ def parse():
     p.add_argument("--ppm", default="", help="also write the headline image there (default: a temporary file)")
     p.add_argument("--size", type=int, default=0, help="override m = n (profiling runs)")
     p.add_argument("--iter-max", type=int, default=0, help="override iterMax (profiling runs)")
-    p.add_argument("--cpu-rows-stride", type=int, default=2)
+    p.add_argument("--cpu-rows-stride", type=int, default=4,
+                   help="the CPU oracle legs (cpu_baseline and --impl reference) time every k-th row of the view")
+    p.add_argument("--cpu-reps", type=int, default=3, help="repetitions of the cpu_baseline row sample")
     return p.parse_args()
 
 
@@ -92,6 +94,16 @@ def bench_view(args):
     if args.size or args.iter_max:
         v = wl.scaled(v, args.size or v.m, args.size or v.n, args.iter_max or v.iter_max)
     return v
+
+
+def bench_config(args, v, ws):
+    """The workload of both arms (ours and --impl reference): the same dict in both JSON lines."""
+    return {"workload": "%dx%d re[-2,1] im[-1.5,1.5] iterMax %d R2 4, %s (tile %d, block %d, unroll %d)"
+                        % (v.m, v.n, v.iter_max, "learned FCFS" if args.sched == "learned" else args.sched,
+                           args.tile, args.block, args.unroll),
+            "l2": "counts %.0f MB per step %s 129 MB L2 (compute-bound)"
+                  % (v.m * v.n * 4 / 1e6, ">" if v.m * v.n * 4 > 129e6 else "<="),
+            "parallelism": "replicas" if ws > 1 else "1 GPU", "bit_exact": "vs FP64 oracle (tests)"}
 
 
 def kernel_sha1():
@@ -184,7 +196,7 @@ def run_reference(args):
     if rank != 0:
         return
     v = bench_view(args)
-    stride = max(args.cpu_rows_stride * 4, 1)
+    stride = max(args.cpu_rows_stride, 1)   # the same row sample as our arm's cpu_baseline
     times, iters, nrows, cores = [], 0, 0, 0
     for k in range(args.warmup + args.steps):
         it, dt, nrows, cores = cpu_sample(v, stride)
@@ -198,7 +210,7 @@ def run_reference(args):
         "impl": "reference", "metric": "Giter/s", "value": val, "unit": "Giter/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "%dx%d re[-2,1] im[-1.5,1.5] iterMax %d R2 4 (row sample)" % (v.m, v.n, v.iter_max)},
+        "config": bench_config(args, v, ws),
         "cpu_baseline": {"value": val, "unit": "Giter/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "Giter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -524,13 +536,8 @@ def run_ours(args):
         "metric": "Giter/s", "value": value, "unit": "Giter/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "%dx%d re[-2,1] im[-1.5,1.5] iterMax %d R2 4, %s (tile %d, block %d, unroll %d)"
-                               % (v.m, v.n, v.iter_max, "learned FCFS" if learned else args.sched, args.tile,
-                                  args.block, args.unroll),
-                   "iterations_per_step": iters,
-                   "l2": "counts %.0f MB per step %s 129 MB L2 (compute-bound)"
-                         % (v.m * v.n * 4 / 1e6, ">" if v.m * v.n * 4 > 129e6 else "<="),
-                   "parallelism": "replicas" if ws > 1 else "1 GPU", "bit_exact": "vs FP64 oracle (tests)"},
+        "config": bench_config(args, v, ws),
+        "iterations_per_step": iters,
         "roofline": roofline_entry(render_iters, kernel_ms, peak, traffic),
         "pct_fp64_peak": 100.0 * value * 1e9 * ALG_OPS_PER_ITER / peak,
         "kernel_ms": kernel_ms,
@@ -629,21 +636,40 @@ def run_ours(args):
             st["giter_s"] = iters / (st["ms"] * 1e-3) / 1e9
             cmp[name] = st
         line["schedulers"] = cmp
-        # the small plain-method view (640 x 480, iterMax 1000, naive rows): launch-bound, reported as is
+        # the small plain-method view (640 x 480, iterMax 1000, naive rows).  With the default grid
+        # (G CTAs) the paper's remainder rule (Sec. III-A) gives floor(480 / G) rows to each CTA and the
+        # m mod G remaining rows to the last one, so the launch is that CTA's serial tail; the paper's
+        # own worker counts N = 2..32 are timed beside it.
         c1 = wl.FULL_VIEW_1
         c1o = torch.empty(c1.m * c1.n, dtype=torch.int32, device=dev)
-        mb.mb_render(c1.window, c1.m, c1.n, c1.iter_max, c1.r2, c1o, sched="naive")
-        a, b = E(), E()
-        a.record(stream)
-        for _ in range(20):
-            mb.mb_render(c1.window, c1.m, c1.n, c1.iter_max, c1.r2, c1o, sched="naive", stream=stream)
-        b.record(stream)
-        b.synchronize()
-        c1ms = a.elapsed_time(b) / 20
+
+        def c1_time(grid):
+            mb.mb_render(c1.window, c1.m, c1.n, c1.iter_max, c1.r2, c1o, sched="naive", grid=grid, stream=stream)
+            a, b = E(), E()
+            a.record(stream)
+            for _ in range(10):
+                mb.mb_render(c1.window, c1.m, c1.n, c1.iter_max, c1.r2, c1o, sched="naive", grid=grid,
+                             stream=stream)
+            b.record(stream)
+            b.synchronize()
+            return a.elapsed_time(b) / 10
+
+        c1ms = c1_time(0)
         mb.mb_sum_counts(c1o, total, stream=stream)
         torch.cuda.synchronize()
-        line["config1_640x480"] = {"sched": "naive", "ms": c1ms, "iterations": int(total.item()),
-                                   "giter_s": int(total.item()) / (c1ms * 1e-3) / 1e9}
+        c1it = int(total.item())
+        per, last = c1.m // g, c1.m // g + c1.m % g
+        workers = {}
+        for nw in (2, 4, 8, 16, 32):
+            ms = c1_time(nw)
+            workers[str(nw)] = {"ms": ms, "giter_s": c1it / (ms * 1e-3) / 1e9,
+                                "rows_per_cta": c1.m // nw, "last_cta_rows": c1.m // nw + c1.m % nw}
+        line["config1_640x480"] = {"sched": "naive", "grid": g, "rows_per_cta": per, "last_cta_rows": last,
+                                   "last_cta_row_share": last / c1.m, "ms": c1ms, "iterations": c1it,
+                                   "giter_s": c1it / (c1ms * 1e-3) / 1e9, "paper_worker_counts": workers,
+                                   "note": "naive rows under the paper's remainder rule: with %d CTAs the last "
+                                           "CTA owns %d of the %d rows, so the launch is its serial tail"
+                                           % (g, last, c1.m)}
         if "naive" in cmp and "learned" in cmp:
             line["learned_vs_naive"] = {"speedup": cmp["naive"]["ms"] / cmp["learned"]["ms"],
                                         "makespan_ratio": cmp["learned"]["makespan_ms"] / cmp["naive"]["makespan_ms"]}
@@ -801,10 +827,15 @@ def run_ours(args):
                                                  for s_, r in tab.items()}}
 
     if not args.no_cpu_baseline:
-        it, dt, nrows, cores = cpu_sample(v, args.cpu_rows_stride)
+        # the same row sample that `--impl reference` times each step, repeated cpu_reps times
+        dts = []
+        for _ in range(max(args.cpu_reps, 1)):
+            it, dt, nrows, cores = cpu_sample(v, max(args.cpu_rows_stride, 1))
+            dts.append(dt)
+        dt = sum(dts) / len(dts)
         line["cpu_baseline"] = {"value": it / dt / 1e9, "unit": "Giter/s", "cores": cores, "kind": "oracle",
-                                "sample": "%d of %d rows (every %d-th), %d iterations, %.1f s"
-                                          % (nrows, v.m, args.cpu_rows_stride, it, dt)}
+                                "sample": "%d of %d rows (every %d-th), %d iterations, mean of %d runs of %.1f s"
+                                          % (nrows, v.m, max(args.cpu_rows_stride, 1), it, len(dts), dt)}
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

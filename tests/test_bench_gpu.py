@@ -32,7 +32,7 @@ def test_bench_json_line_contract():
     assert "1024x1024" in c["workload"] and "iterMax 2000" in c["workload"] and "learned FCFS" in c["workload"]
     assert "4 MB per step <= 129 MB L2" in c["l2"]
     # value = iterations per step / time per step
-    assert d["value"] == pytest.approx(c["iterations_per_step"] / d["ms_per_step"] / 1e6, rel=1e-6)
+    assert d["value"] == pytest.approx(d["iterations_per_step"] / d["ms_per_step"] / 1e6, rel=1e-6)
     r = d["roofline"]
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["peak"] > 0 and r["achieved"] > 0
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], rel=1e-9)

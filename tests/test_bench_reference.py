@@ -22,6 +22,9 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "Giter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert "256x256" in d["config"]["workload"] and "iterMax 500" in d["config"]["workload"]
+    # the same config dict our arm prints, and the same row sample as our cpu_baseline
+    assert set(d["config"]) == {"workload", "l2", "parallelism", "bit_exact"}
+    assert "every 4-th" in d["cpu_baseline"]["sample"]
 
 
 def test_reference_arm_under_torchrun_prints_once():
