@@ -416,6 +416,25 @@ int mb_colorize(const uint32_t* counts, uint64_t count, uint32_t iter_max, uint8
 /* Writes a binary PPM (P6, maxval 255) of m rows x n columns from rgb (host). */
 int mb_write_ppm(const char* path, const uint8_t* rgb, uint32_t m, uint32_t n);
 
+/* ---- the master gather of one image rendered by several workers (Sec. III-A/B) ----
+ * Each worker renders the items it was dealt (first come, first served across
+ * GPUs) into its own image; only those pixels are sent to the master, which
+ * writes them into its image.  Layout of `packed`: one slot of tile*tile counts
+ * per item, item k at offset k*tile*tile, its rows row0..row0+rows-1 at their
+ * row offset within the slot, tile counts per row.  Pixels outside the image
+ * and slot rows outside the item are not written (pack) or not read (unpack).
+ *   img     device, m*n counts, row-major (read by pack, written by unpack)
+ *   items   device, n_items entries (tile < tiles of the image, row0+rows <= tile;
+ *           an entry that is not sets bit 2 of *status, when given, and is skipped)
+ *   packed  device, n_items*tile*tile counts
+ *   tile    power of two in [8, 256]; m, n in [1, 2^20]
+ * Asynchronous on `stream`; nothing is allocated.  Errors: MB_EINVAL (null
+ * pointers, bad sizes), MB_ECUDA. */
+int mb_pack_items(const uint32_t* img, uint32_t m, uint32_t n, uint32_t tile, const mb_item* items,
+                  uint32_t n_items, uint32_t* packed, uint32_t* status, void* stream);
+int mb_unpack_items(const uint32_t* packed, uint32_t m, uint32_t n, uint32_t tile, const mb_item* items,
+                    uint32_t n_items, uint32_t* img, uint32_t* status, void* stream);
+
 /* FP64 issue-rate microbenchmark (not in the paper; the measurement's
  * denominator): runs independent chains of one binary64
  * operation (op: 0 = add, 1 = mul, 2 = fma) on every SM and returns the

@@ -439,6 +439,23 @@ def mb_colorize(counts, iter_max, rgb, stream=None):
            "mb_colorize")
 
 
+# ---- master gather of a sharded image ---------------------------------------------------
+
+def mb_pack_items(img, m, n, tile, items, packed, n_items=None, status=None, stream=None):
+    """Pixels of the listed items (int32 [K, 2] device tensor of (tile, row0 | rows << 16))
+    of the m x n device image into `packed` (one tile*tile slot per item)."""
+    k = int(items.shape[0]) if n_items is None else int(n_items)
+    _check(_L().lib().mb_pack_items(_ptr(img), int(m), int(n), int(tile), _ptr(items), k, _ptr(packed),
+                                    _ptr(status), _stream(stream)), "mb_pack_items")
+
+
+def mb_unpack_items(packed, m, n, tile, items, img, n_items=None, status=None, stream=None):
+    """Inverse of mb_pack_items: writes the packed items' pixels into the image."""
+    k = int(items.shape[0]) if n_items is None else int(n_items)
+    _check(_L().lib().mb_unpack_items(_ptr(packed), int(m), int(n), int(tile), _ptr(items), k, _ptr(img),
+                                      _ptr(status), _stream(stream)), "mb_unpack_items")
+
+
 def mb_write_ppm(path, rgb_host, m, n):
     """Binary PPM from host RGB bytes (numpy array or CPU tensor, m*n*3)."""
     ptr = rgb_host.ctypes.data if hasattr(rgb_host, "ctypes") else rgb_host.data_ptr()

@@ -93,6 +93,10 @@ def _load():
     L.mb_colorize.restype = i32
     L.mb_write_ppm.argtypes = [ctypes.c_char_p, vp, u32, u32]
     L.mb_write_ppm.restype = i32
+    L.mb_pack_items.argtypes = [vp, u32, u32, u32, vp, u32, vp, vp, vp]
+    L.mb_pack_items.restype = i32
+    L.mb_unpack_items.argtypes = [vp, u32, u32, u32, vp, u32, vp, vp, vp]
+    L.mb_unpack_items.restype = i32
     L.mb_selftest_products.restype = i32
     L.mb_device_info.restype = i32
     P = ctypes.POINTER

@@ -26,7 +26,7 @@ def test_bench_json_line_contract():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["metric"] == "Giter/s" and d["unit"] == "Giter/s" and d["higher_is_better"] is True
-    assert d["n_gpus"] == 1 and d["steps"] == 2 and d["warmup"] == 3 and d["scaling"] == "weak"
+    assert d["n_gpus"] == 1 and d["steps"] == 2 and d["warmup"] == 3 and d["scaling"] == "strong"
     assert d["vs_baseline"] is None and d["dtype"] == "f64" and d["data"] == "synthetic"
     c = d["config"]
     assert "1024x1024" in c["workload"] and "iterMax 2000" in c["workload"] and "learned FCFS" in c["workload"]

@@ -1,6 +1,8 @@
-"""Multi-GPU partition logic on the CPU: two gloo ranks split the tiles of a
-view and a longest-first item list; their shares are disjoint and cover
-everything, and the timing rule takes the max over ranks."""
+"""Multi-GPU partition logic on the CPU (gloo ranks as processes): the static
+tile deal, and the first-come-first-served render of one image -- chunks of
+the item list handed out by the master's store counter, the packed gather to
+rank 0 -- with one rank slowed on the host, so that it takes fewer chunks,
+and the assembled image equal to the oracle's."""
 import os
 import socket
 
@@ -82,35 +84,99 @@ def _fake_render(window, m, n, iter_max, r2, out, items, tile):
         img[r0:r1, c0:c1] = torch.from_numpy(full[r0:r1, c0:c1])
 
 
-def _sharded_worker(rank, world, port, q):
+def _item_pixels(m, n, tile, t, packed):
+    """(image index, slot offset) pairs of one item, pixels inside the image only."""
+    row0, rows = packed & 0xFFFF, (packed >> 16) & 0xFFFF
+    tiles_x = -(-n // tile)
+    ty, tx = divmod(t, tiles_x)
+    for r in range(row0, row0 + rows):
+        for c in range(tile):
+            i, j = ty * tile + r, tx * tile + c
+            if i < m and j < n:
+                yield i * n + j, r * tile + c
+
+
+def _fake_pack(img, m, n, tile, items, packed):
+    """Stand-in for mb_pack_items in this CPU test (the layout of include/mb.h)."""
+    for k, (t, p) in enumerate(items.tolist()):
+        for at, off in _item_pixels(m, n, tile, t, p):
+            packed[k * tile * tile + off] = img[at]
+
+
+def _fake_unpack(packed, m, n, tile, items, img):
+    for k, (t, p) in enumerate(items.tolist()):
+        for at, off in _item_pixels(m, n, tile, t, p):
+            img[at] = packed[k * tile * tile + off]
+
+
+VIEW = ((-2.0, 1.0, -1.0, 1.0), 70, 101, 400, 4.0)
+
+
+def _sharded_worker(rank, world, port, slow_rank, q):
+    import time
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
-    dist.init_process_group("gloo", rank=rank, world_size=world)
-    img = shard.render_sharded((-2.0, 1.0, -1.0, 1.0), 70, 101, 400, 4.0, tile=16, render=_fake_render)
+    store = shard.make_store(rank, world)
+    dist.init_process_group("gloo", store=store, rank=rank, world_size=world)
+
+    def slow(r, c):
+        if r == slow_rank:
+            time.sleep(0.25)
+
+    stats = {}
+    img = shard.render_sharded(*VIEW, tile=16, chunk=2, store=store, render=_fake_render, pack=_fake_pack,
+                               unpack=_fake_unpack, after_chunk=slow, stats=stats)
+    # a second image in the same job uses a fresh counter
+    img2 = shard.render_sharded(*VIEW, tile=8, store=store, render=_fake_render, pack=_fake_pack,
+                                unpack=_fake_unpack)
     dist.barrier()
     dist.destroy_process_group()
-    q.put((rank, None if img is None else img.numpy().copy()))
+    q.put((rank, None if img is None else img.numpy().copy(), None if img2 is None else img2.numpy().copy(),
+           stats))
 
 
 @pytest.mark.parametrize("world", [2, 3])
-def test_sharded_render_assembles_the_image(world):
-    """Ranks render disjoint tile shards of a ragged 70 x 101 view; the
-    sum-reduce on rank 0 is exactly the oracle's full image."""
+def test_fcfs_sharded_render_assembles_the_image(world):
+    """Ranks take chunks of a ragged 70 x 101 view first come first served;
+    rank 1 is slowed on the host and takes fewer chunks; the packed gather on
+    rank 0 is exactly the oracle's full image."""
     import numpy as np
     import oracle
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_sharded_worker, args=(r, world, port, q)) for r in range(world)]
+    procs = [ctx.Process(target=_sharded_worker, args=(r, world, port, 1, q)) for r in range(world)]
     for p in procs:
         p.start()
-    res = dict(q.get(timeout=180) for _ in range(world))
+    res = {r: (a, b, st) for r, a, b, st in (q.get(timeout=300) for _ in range(world))}
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    want = oracle.render((-2.0, 1.0, -1.0, 1.0), 70, 101, 400, 4.0)
-    assert np.array_equal(res[0].view(np.uint32).reshape(70, 101), want)
-    assert all(res[r] is None for r in range(1, world))
+    want = oracle.render(*VIEW)
+    assert np.array_equal(res[0][0].view(np.uint32).reshape(70, 101), want)
+    assert np.array_equal(res[0][1].view(np.uint32).reshape(70, 101), want)
+    assert all(res[r][0] is None and res[r][1] is None for r in range(1, world))
+    chunks = [res[r][2]["chunks"] for r in range(world)]
+    n_tiles = (-(-101 // 16)) * (-(-70 // 16))
+    allc = sorted(c for part in chunks for c in part)
+    assert allc == list(range(-(-n_tiles // 2)))                # every chunk once
+    assert len(chunks[1]) < len(chunks[0])                     # the slow rank took fewer
+    assert sum(res[r][2]["items"] for r in range(world)) == n_tiles
+
+
+def test_dispatcher_hands_out_each_chunk_once():
+    store = dist.HashStore()
+    d = shard.ChunkDispatcher(store, "k", 10, 3)
+    got = []
+    while True:
+        x = d.next()
+        if x is None:
+            break
+        got.append(x)
+    assert got == [(0, 0, 3), (1, 3, 6), (2, 6, 9), (3, 9, 10)]
+    assert d.next() is None
+    with pytest.raises(ValueError):
+        shard.ChunkDispatcher(store, "k", 10, 0)
 
 
 def test_tile_items_cover_whole_tiles():
