@@ -7,9 +7,10 @@ tile features, MLP cost prediction, longest-first order with splits, and the
 FCFS render of the rest -- with every count bit-identical to the FP64 oracle.
 Giter/s = (sum of counts, i.e. z-updates) / step time.  The roofline is the
 FP64 pipe, measured in this run by the library's own microbenchmark
-(mb_fp64_peak): a step's 8 nominal binary64 operations take 3 FP64-pipe
-issues (the products are formed exactly on the integer pipes), so the
-attainable rate is the measured issue rate x 8/3.
+(mb_fp64_peak): a step's 8 nominal binary64 operations take 2.5 FP64-pipe
+issues on average (the products, the doubling and every other subtraction
+are formed exactly on the integer pipes), so the attainable rate is the
+measured issue rate x 8/2.5.
 
 Beside the headline (outside the timed region, rank 0 only): the paper's three
 row schedulers and plain tile FCFS on the same view (makespan, idle tail), the
@@ -17,10 +18,13 @@ end-to-end figure through host buffers, the paper's computation / total timing
 with the PPM file, the 640 x 480 naive view, the binary32 and double-float
 variants (their own rates and how many pixels differ from binary64), exact
 cycle detection (time to the identical image), the CPU oracle on a row sample,
-the 256-viewport batch as a replayed CUDA graph, and a short Poisson serving
-run (p50 / p99 latency), plain and with cycle detection.  --zoom adds the
-16384^2 deep-zoom comparison, --table2 the GPU analogue of the paper's Table II
-and --serve-sweep a sweep of request rates.
+the 256-viewport batch as a replayed CUDA graph (default and learned queue
+order), a short Poisson serving run (p50 / p99 latency), plain and with cycle
+detection, the 16384^2 deep-zoom comparison (learned vs plain FCFS), and a
+serving sweep over request rates that replays one fixed draw of requests.
+--table2 adds the GPU analogue of the paper's Table II.  Under torchrun
+(--gpus N > 1) the step is one image rendered over the N GPUs, first come
+first served (see run_sharded).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -37,7 +41,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 ALG_OPS_PER_ITER = 8  # binary64 operations per escape step: 3 mul, 1 doubling, 4 add/sub
-FP64_PIPE_OPS_PER_ITER = 3  # of which issued on the FP64 pipe: the 3 additions (products on the integer pipes)
+# of which issued on the FP64 pipe, on average: the 3 additions of a step, less the subtraction that
+# every other step does exactly on the integer pipes (products and doubling are always there)
+FP64_PIPE_OPS_PER_ITER = 2.5
 
 # DRAM traffic of the main render kernel from the ncu capture summarised in
 # profiles/render_kernel_list_8192x8192_it1000.md (dram read + write per launch
@@ -68,11 +74,14 @@ def parse():
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-precision", action="store_true", help="skip the binary32 / double-float variants")
     p.add_argument("--no-cycle", action="store_true", help="skip the exact-cycle-detection timing")
-    p.add_argument("--zoom", action="store_true", help="add the 16384^2 deep-zoom comparison (about a minute)")
+    p.add_argument("--no-zoom", action="store_true", help="skip the 16384^2 deep-zoom comparison (about a minute)")
     p.add_argument("--table2", action="store_true",
                    help="add the GPU analogue of the paper's Table II: speed-up over one worker (CTA) of the "
                         "naive, alternating and FCFS row schemes on the paper's test shape (2000^2 sample)")
-    p.add_argument("--serve-sweep", default="", help="comma-separated request rates for a serving sweep")
+    p.add_argument("--serve-sweep", default="10,20,40,80,200,1000",
+                   help="comma-separated request rates (1/s) of the serving sweep ('' = none); one fixed draw of "
+                        "--serve-sweep-count requests is replayed at every rate")
+    p.add_argument("--serve-sweep-count", type=int, default=200)
     p.add_argument("--serve-count", type=int, default=100)
     p.add_argument("--ppm", default="", help="also write the headline image there (default: a temporary file)")
     p.add_argument("--size", type=int, default=0, help="override m = n (profiling runs)")
@@ -246,15 +255,21 @@ def pct(xs, q):
     return xs[k]
 
 
-def run_serve(mb, wl, torch, rate, count, seed_shift=0, **sopts):
+def run_serve(mb, wl, torch, rate, count, views=None, **sopts):
     """Open-loop Poisson stream of batch-distribution viewports into a server with a
-    40 GB budget; latency percentiles (submit to done) and delivered Giter/s."""
-    views = wl.batch_views(count=count, seed=wl.SEED + 500 + seed_shift)
-    arrivals = wl.poisson_arrivals(rate, count)
+    40 GB budget; latency percentiles (submit to done) and delivered Giter/s.
+    `views` (default: a seeded draw of `count`) arrive at the times of one seeded
+    unit-rate Poisson stream divided by `rate`, so that runs at different rates
+    replay the same requests in the same pattern, only faster or slower."""
+    if views is None:
+        views = wl.batch_views(count=count, seed=wl.SEED + 500)
+    count = len(views)
+    arrivals = [t / rate for t in wl.poisson_arrivals(1.0, count)]
     srv = mb.Server(budget_bytes=40 << 30, queue_limit=4096, **sopts)
     ids, lat, iters, failed = [None] * count, [], 0, 0
     tot = torch.zeros(1, dtype=torch.int64, device="cuda")
     side = torch.cuda.Stream()
+    max_queued = 0
     t0 = time.perf_counter()
     for k, (v, ta) in enumerate(zip(views, arrivals)):
         d = t0 + ta - time.perf_counter()
@@ -264,6 +279,8 @@ def run_serve(mb, wl, torch, rate, count, seed_shift=0, **sopts):
             ids[k] = srv.submit(v)
         except mb.MBError:
             failed += 1
+        if k % 8 == 0:
+            max_queued = max(max_queued, srv.counters()["queued"])
     t_first, t_last = None, 0
     for k, rid in enumerate(ids):
         if rid is None:
@@ -282,9 +299,11 @@ def run_serve(mb, wl, torch, rate, count, seed_shift=0, **sopts):
     c = srv.counters()
     srv.destroy()
     span = (t_last - t_first) / 1e9 if t_first is not None else 0.0
-    return {"rate_per_s": rate, "requests": count, "completed": len(lat), "rejected_or_failed": failed,
+    offered = iters / arrivals[-1] / 1e9 if arrivals and arrivals[-1] > 0 else None
+    return {"rate_per_s": rate, "requests": count, "submitted": c["submitted"], "admitted": c["admitted"],
+            "completed": len(lat), "rejected_or_failed": failed, "max_queued": max_queued,
             "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "giter_s": iters / span / 1e9 if span else None,
-            "iterations": iters, "rounds": c["rounds"], "peak_gb": c["peak_bytes"] / 1e9,
+            "offered_giter_s": offered, "iterations": iters, "rounds": c["rounds"], "peak_gb": c["peak_bytes"] / 1e9,
             "budget_gb": 40 * 2 ** 30 / 1e9}
 
 
@@ -348,21 +367,25 @@ def measured_hbm_gbs():
 def roofline_entry(steps, kernel_ms, peak, traffic):
     """Roofline of the main render launch: `steps` escape steps in `kernel_ms`,
     against the FP64-pipe issue rate `peak` (binary64 ops/s) measured in this run.
-    The binding pipe is FP64, which each step uses for its 3 additions only, so
-    the attainable rate of the step's 8 nominal binary64 ops is peak x 8/3."""
+    The FP64 pipe carries 2.5 of a step's 8 nominal binary64 ops on average (the
+    three additions, less the subtraction of every other step, which runs exactly
+    on the integer pipes), so the attainable rate of the 8 ops is peak x 8/2.5,
+    as long as the integer pipes keep up (they are co-saturated: ncu shows FP64
+    ~80 % and integer ALU ~80 % busy)."""
     step_peak = peak * ALG_OPS_PER_ITER / FP64_PIPE_OPS_PER_ITER
     achieved = steps * ALG_OPS_PER_ITER / (kernel_ms * 1e-3)
     return {"bound": "alu", "achieved": achieved / 1e12, "peak": step_peak / 1e12, "unit": "TFLOP/s",
             "frac": achieved / step_peak, "traffic": traffic,
             "peak_source": ("derived from measured (of measured): the FP64-pipe issue rate measured now "
-                            "by mb_fp64_peak (%.4f T binary64 ops/s) x 8/3 -- each escape step's 8 "
-                            "nominal binary64 ops need 3 FP64-pipe issues (its additions); the three "
-                            "products run exactly on the integer pipes, which are not the binding "
-                            "pipe (ncu: FP64 84 %%, integer ALU 78 %% busy)" % (peak / 1e12)),
+                            "by mb_fp64_peak (%.4f T binary64 ops/s) x 8/2.5 -- an escape step's 8 "
+                            "nominal binary64 ops need 2.5 FP64-pipe issues on average (its three "
+                            "additions, less the subtraction that every other step does on the integer "
+                            "pipes); the products and the doubling run exactly on the integer pipes, "
+                            "which are co-saturated with the FP64 pipe" % (peak / 1e12)),
             "fp64_pipe_frac": FP64_PIPE_OPS_PER_ITER * steps / (kernel_ms * 1e-3) / peak,
             "nominal_frac": achieved / peak,
             "nominal_note": "8 nominal ops per step over the plain FP64-pipe peak (the metric's "
-                            "'% of FP64 peak' form, above 1 because 5 of the 8 ops are not FP64-pipe "
+                            "'% of FP64 peak' form, above 1 because 5.5 of the 8 ops are not FP64-pipe "
                             "instructions)",
             "kernel": "render_kernel (main FCFS render, CUDA events around its launch)",
             "algorithmic": "8 binary64 ops per escape step x %d steps per launch" % steps,
@@ -522,7 +545,7 @@ def run_sharded(args, ws, rank, local):
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": step_peak / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / step_peak, "traffic": None,
                      "kernel": "whole sharded step (all chunks' render launches plus the gather) over %d GPUs" % ws,
-                     "peak_source": "derived from measured (of measured): %d x mb_fp64_peak x 8/3" % ws},
+                     "peak_source": "derived from measured (of measured): %d x mb_fp64_peak x 8/2.5" % ws},
         "clocks": clocks,
         "chunks_per_rank": [int(x.item()) / args.steps for x in per_rank],
         "e2e": {"value": iters / (float(et.item()) * 1e-3) / 1e9, "unit": "Giter/s", "h2d_bytes_per_step": 0,
@@ -827,11 +850,17 @@ def run_ours(args):
             sc["note"] = ("cycle_check=1: identical counts; detected pixels skip their remaining steps, so "
                           "only latency and completions are reported")
             line["serve_cycle_check"] = sc
-    if args.serve_sweep:
-        line["serve_sweep"] = [run_serve(mb, wl, torch, float(r), args.serve_count, k)
-                               for k, r in enumerate(args.serve_sweep.split(","))]
+    if args.serve_sweep and not args.no_serve:
+        # one fixed draw of requests, replayed at every rate (only the arrival times scale)
+        sweep_views = wl.batch_views(count=args.serve_sweep_count, seed=wl.SEED + 600)
+        runs = [run_serve(mb, wl, torch, float(r), args.serve_sweep_count, views=sweep_views)
+                for r in args.serve_sweep.split(",")]
+        line["serve_sweep"] = {"requests_per_rate": args.serve_sweep_count, "draw": "batch_views(seed=SEED+600)",
+                               "note": "offered_giter_s = rate x mean iterations per request; below the render "
+                                       "rate the arrivals bound the delivered Giter/s, above it queueing sets p99",
+                               "rates": runs}
 
-    if args.zoom:
+    if not args.no_zoom:
         z = wl.ZOOM_3
         zo = torch.empty(z.m * z.n, dtype=torch.int32, device=dev)
         zparams = tilemodel.default_model(tile=64)[0] if params is not None else None

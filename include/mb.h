@@ -138,6 +138,14 @@ typedef struct {
                                 paper.  Honoured by mb_render, mb_render_batch, mb_batch_plan_create and
                                 mb_serve_create (binary64 only, not with fp64_products); the other entry points
                                 return MB_EINVAL for it; 0 = off */
+  uint32_t learned_order;    /* mb_render_batch / mb_batch_plan_create: 1 = queue the (view, tile) items of all
+                                views longest-first by predicted cost, with heavy tiles split into row strips (the
+                                order-and-split rule of mb_order_split over the batch's tiles, split divisor
+                                `split`), instead of decreasing iterMax then raster order; the costs come from a
+                                probe of every view (8 x 8 samples per tile, tile >= 16) run once when the plan is
+                                built, and from `model` (or, when model is NULL, the probe-sum estimate).
+                                Scheduling only: the counts are unchanged.  0 = off */
+  const float* model;        /* device, MB_MLP_PARAMS floats: the tile-cost network for learned_order; may be NULL */
 } mb_opts;
 
 /* Library version string (not in the paper). */
@@ -450,6 +458,14 @@ int mb_fp64_peak(int op, double* ops_per_s, double* seconds);
  * kernels replay the step on the FP64 pipe instead.  Device arrays. */
 int mb_selftest_products(const double* a, const double* b, uint64_t n, double* sq, double* pr, uint8_t* ok,
                          void* stream);
+
+/* Self-test of the integer-pipe subtraction used by every other binary64 escape
+ * step (not in the paper): for i < n, d[i] = RN(a[i] - b[i]) as the kernels form
+ * it, for positive normal a[i], b[i] (the squares of a step), and ok[i] = 1 when
+ * that result is exact; ok[i] = 0 (the kernels then replay the step on the FP64
+ * pipe) when the exponents differ by more than 31 or the leading 32 bits of
+ * the aligned mantissas cancel.  Device arrays. */
+int mb_selftest_psub(const double* a, const double* b, uint64_t n, double* d, uint8_t* ok, void* stream);
 
 /* Self-test of the bounded wait in the work-claiming protocol (not in the
  * paper; the failure-detection test of the render kernels).  Launches `ctas`

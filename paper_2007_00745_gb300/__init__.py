@@ -59,7 +59,7 @@ def _stream(stream):
 def _opts(sched="fcfs_tiles", tile=0, grid=0, block=0, unroll=0, stream=None, items=None, n_items=0,
           tile_totals=None, trace=None, trace_len=0, status=None, workspace=None, workspace_bytes=0,
           events=None, fp64_products=0, max_seconds=None, split=0, round_tiles=0, precision="fp64",
-          cycle_check=0):
+          cycle_check=0, learned_order=0, model=None):
     L = _L()
     o = L.mb_opts()
     o.sched = SCHEDS[sched] if isinstance(sched, str) else int(sched)
@@ -78,6 +78,8 @@ def _opts(sched="fcfs_tiles", tile=0, grid=0, block=0, unroll=0, stream=None, it
     o.round_tiles = int(round_tiles)
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.cycle_check = int(cycle_check)
+    o.learned_order = int(learned_order)
+    o.model = _ptr(model)
     if events is not None:   # (start, stop) torch.cuda.Event pair recorded around the main render kernel
         handles = []
         for ev in events:
@@ -199,6 +201,12 @@ def mb_selftest_products(a, b, sq, pr, ok, stream=None):
     """Integer-pipe products of the render kernels on device arrays (see include/mb.h)."""
     _check(_L().lib().mb_selftest_products(_ptr(a), _ptr(b), int(a.numel()), _ptr(sq), _ptr(pr), _ptr(ok),
                                            _stream(stream)), "mb_selftest_products")
+
+
+def mb_selftest_psub(a, b, d, ok, stream=None):
+    """Integer-pipe subtraction of the render kernels on device arrays (see include/mb.h)."""
+    _check(_L().lib().mb_selftest_psub(_ptr(a), _ptr(b), int(a.numel()), _ptr(d), _ptr(ok), _stream(stream)),
+           "mb_selftest_psub")
 
 
 def mb_device_info(block=0):

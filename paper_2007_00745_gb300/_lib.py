@@ -34,7 +34,7 @@ class mb_opts(ctypes.Structure):
                 ("stream", vp), ("items", vp), ("n_items", u32), ("tile_totals", vp), ("trace", vp), ("trace_len", u32),
                 ("status", vp), ("workspace", vp), ("workspace_bytes", sz), ("split", u32), ("round_tiles", u32), ("max_seconds", u32), ("fp64_products", u32),
                 ("ev_start", vp), ("ev_stop", vp), ("precision", u32),
-                ("cycle_check", u32)]
+                ("cycle_check", u32), ("learned_order", u32), ("model", vp)]
 
 
 class mb_view(ctypes.Structure):
@@ -98,6 +98,8 @@ def _load():
     L.mb_unpack_items.argtypes = [vp, u32, u32, u32, vp, u32, vp, vp, vp]
     L.mb_unpack_items.restype = i32
     L.mb_selftest_products.restype = i32
+    L.mb_selftest_psub.argtypes = [vp, vp, u64, vp, vp, vp]
+    L.mb_selftest_psub.restype = i32
     L.mb_device_info.restype = i32
     P = ctypes.POINTER
     L.mb_probe.argtypes = [P(mb_window), u32, u32, u32, f64, vp, vp, P(mb_opts)]

@@ -58,6 +58,15 @@ __global__ void selftest_products_kernel(const double* __restrict__ a, const dou
   }
 }
 
+__global__ void selftest_psub_kernel(const double* __restrict__ a, const double* __restrict__ b, uint64_t n,
+                                     double* __restrict__ d, uint8_t* __restrict__ ok) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    bool odd = false;
+    d[i] = emul_psub(a[i], b[i], odd);
+    ok[i] = (uint8_t)!odd;
+  }
+}
+
 // Bounded-wait self-test of the CTA work-claiming protocol: the CTA's work word
 // says its item (a 64-pixel raster tile) is already claimed past its end, and
 // no worker will ever publish the next item -- the producer is gone.  Every warp
@@ -101,6 +110,15 @@ extern "C" int mb_selftest_products(const double* a, const double* b, uint64_t n
   uint64_t blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   selftest_products_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(a, b, n, sq, pr, ok);
+  return cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
+}
+
+extern "C" int mb_selftest_psub(const double* a, const double* b, uint64_t n, double* d, uint8_t* ok, void* stream) {
+  if (!a || !b || !d || !ok) return MB_EINVAL;
+  if (n == 0) return MB_OK;
+  uint64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  selftest_psub_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(a, b, n, d, ok);
   return cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
 }
 

@@ -2,10 +2,15 @@
 //
 // Every view gets its Cx / Cy arrays (Sec. III-A) in one pixel-map launch (one
 // grid row per view); the render is one first-come-first-served launch
-// (Sec. III-B) over a list of (view, tile) items.  Views are queued in order of
-// decreasing iteration budget (a cost bound known before rendering), tiles of
-// a view in raster order.  A plan owns its device memory and a captured graph
-// of the two launches, so replaying a batch costs one cudaGraphLaunch.
+// (Sec. III-B) over a list of (view, tile) items.  By default views are queued
+// in order of decreasing iteration budget (a cost bound known before
+// rendering), tiles of a view in raster order.  With opts->learned_order the
+// queue is built once, when the plan is made, from predicted tile costs: every
+// view is probed (8 x 8 samples per tile), the tile-cost network (or the
+// probe-sum estimate) predicts each tile's cost, and the tiles of all views are
+// queued longest-first with heavy tiles split into row strips.  A plan owns
+// its device memory and a captured graph of the two launches, so replaying a
+// batch costs one cudaGraphLaunch.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -28,6 +33,8 @@ struct mb_batch_plan {
   size_t bytes = 0;
   mb::ViewDesc* views = nullptr;
   mb::BatchItem* items = nullptr;
+  mb::BatchItem* litems = nullptr;  // the learned queue (owned; items points to it when in use)
+  uint32_t learned = 0;
   uint32_t* counter = nullptr;
   uint32_t* status = nullptr;
   mb::RenderFn fn = nullptr;
@@ -59,6 +66,93 @@ __global__ void batch_items_kernel(const uint32_t* __restrict__ prefix, const ui
     it.rows = (uint16_t)tile;
     items[g] = it;
   }
+}
+
+// Learned queue: global tile g of the batch (views in index order, goff[v] = first
+// global tile of view v) -> (view, tile within the view), keeping the strip.
+__global__ void batch_learned_items_kernel(const mb_item* __restrict__ in, uint32_t n, const uint32_t* __restrict__ goff,
+                                           uint32_t nviews, BatchItem* __restrict__ out) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    mb_item e = in[k];
+    uint32_t lo = 0, hi = nviews;  // largest v with goff[v] <= g
+    while (hi - lo > 1) {
+      uint32_t mid = (lo + hi) / 2;
+      if (goff[mid] <= e.tile) lo = mid;
+      else hi = mid;
+    }
+    BatchItem b;
+    b.view = lo;
+    b.tile = e.tile - goff[lo];
+    b.row0 = e.row0;
+    b.rows = e.rows;
+    out[k] = b;
+  }
+}
+
+// Build the learned queue of a plan (see the file comment).  Leaves the default
+// queue in place when the list would not fit its capacity.
+static int batch_learned_queue(const mb_view* views, uint32_t count, const mb_opts* opt, mb_batch_plan* P) {
+  const uint32_t tile = P->tile;
+  if (tile < 16) return MB_EINVAL;
+  std::vector<uint32_t> goff(count + 1, 0);
+  for (uint32_t i = 0; i < count; ++i)
+    goff[i + 1] = goff[i] + ((views[i].n + tile - 1) / tile) * ((views[i].m + tile - 1) / tile);
+  const uint32_t nt = goff[count];
+  const uint32_t split = opt->split ? (opt->split > 4096 ? 4096u : opt->split) : 4u;
+  uint64_t cap64 = 2ull * nt + 4ull * split * P->grid + 1024;
+  if (cap64 > 16ull * nt) cap64 = 16ull * nt;
+  if (cap64 >= 0xFFFFFFF0ull) return MB_EINVAL;
+  const uint32_t cap = (uint32_t)cap64;
+  size_t o_probe = 0, o_feat = b256((size_t)nt * 64 * 4);
+  size_t o_items = o_feat + (opt->model ? b256((size_t)nt * MB_MLP_FEATURES * 4) : 0);
+  size_t o_n = o_items + b256((size_t)cap * sizeof(mb_item));
+  size_t o_goff = o_n + 256, total = o_goff + b256((size_t)(count + 1) * 4);
+  char* tmp = nullptr;
+  if (cudaMalloc((void**)&tmp, total) != cudaSuccess) {
+    cudaGetLastError();
+    return MB_ENOMEM;
+  }
+  uint32_t* probe = (uint32_t*)(tmp + o_probe);
+  float* feat = opt->model ? (float*)(tmp + o_feat) : nullptr;
+  mb_item* li = (mb_item*)(tmp + o_items);
+  uint32_t* dn = (uint32_t*)(tmp + o_n);
+  mb_opts po;
+  std::memset(&po, 0, sizeof po);
+  po.tile = tile;
+  po.block = P->block;
+  po.unroll = P->unroll;
+  int rc = MB_OK;
+  for (uint32_t i = 0; i < count && rc == MB_OK; ++i) {
+    const mb_view& q = views[i];
+    rc = mb_probe(&q.w, q.m, q.n, q.iter_max, q.escape_r2, probe + (size_t)goff[i] * 64, nullptr, &po);
+    if (rc == MB_OK && feat)
+      rc = mb_tile_features(probe + (size_t)goff[i] * 64, &q.w, q.m, q.n, q.iter_max, tile,
+                            feat + (size_t)goff[i] * MB_MLP_FEATURES, nullptr);
+  }
+  if (rc == MB_OK) rc = order_tiles(probe, feat, nt, opt->model, tile, P->grid, split, li, cap, dn, nullptr, nullptr);
+  uint32_t n = 0;
+  if (rc == MB_OK && cudaMemcpy(&n, dn, 4, cudaMemcpyDeviceToHost) != cudaSuccess) rc = MB_ECUDA;
+  if (rc == MB_OK && n > 0) {
+    if (cudaMalloc((void**)&P->litems, (size_t)n * sizeof(BatchItem)) != cudaSuccess) {
+      cudaGetLastError();
+      rc = MB_ENOMEM;
+    }
+    if (rc == MB_OK &&
+        cudaMemcpy(tmp + o_goff, goff.data(), (count + 1) * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = MB_ECUDA;
+    if (rc == MB_OK) {
+      uint32_t nb = (uint32_t)std::min<uint64_t>((n + 255) / 256, 4096);
+      batch_learned_items_kernel<<<nb, 256>>>(li, n, (const uint32_t*)(tmp + o_goff), count, P->litems);
+      if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) rc = MB_ECUDA;
+    }
+    if (rc == MB_OK) {
+      P->items = P->litems;
+      P->n_items = n;
+      P->learned = 1;
+    }
+  }
+  cudaFree(tmp);
+  return rc;
 }
 
 struct BatchLayout {
@@ -157,6 +251,7 @@ static int batch_prepare(const mb_view* views, uint32_t count, const mb_opts* op
                                     : render_fn(KIND_BATCH, S_FCFS, filt, (int)P->unroll);
   P->grid = opt && opt->grid ? opt->grid : default_grid(P->fn, P->block);
   (void)graph;
+  if (opt && opt->learned_order) return batch_learned_queue(views, count, opt, P);
   return MB_OK;
 }
 
@@ -187,6 +282,7 @@ static void plan_free(mb_batch_plan* P) {
   if (P->graph) cudaGraphDestroy(P->graph);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   if (P->dmem) cudaFree(P->dmem);
+  if (P->litems) cudaFree(P->litems);
   delete P;
 }
 
@@ -275,6 +371,7 @@ static uint64_t batch_key(const mb_view* views, uint32_t count, uint32_t stride,
   }
   h = fnv1a(&base.precision, 4, h);    // the arithmetic changes the best launch shape
   h = fnv1a(&base.cycle_check, 4, h);
+  h = fnv1a(&base.learned_order, 4, h);
   return fnv1a(&stride, 4, h);
 }
 

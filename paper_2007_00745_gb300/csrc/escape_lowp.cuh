@@ -92,7 +92,7 @@ __device__ __forceinline__ void f32_iter(float& zr, float& zi, float cr, float c
 }
 
 template <bool FILT, bool EMUL>
-__device__ __forceinline__ void step(LaneF32& L, double, EscThr) {
+__device__ __forceinline__ void step(LaneF32& L, double, EscThr, bool = false) {
 #pragma unroll
   for (int k = 0; k < F32_ITERS; ++k) {
     bool e;
@@ -208,7 +208,7 @@ __device__ __forceinline__ void lane_start(LaneF2& L, double cr, double ci, uint
 __device__ __forceinline__ void block_begin(LaneF2&) {}
 
 template <bool FILT, bool EMUL>
-__device__ __forceinline__ void step(LaneF2& L, double, EscThr) {
+__device__ __forceinline__ void step(LaneF2& L, double, EscThr, bool = false) {
   F2 zr2 = f2_mul(L.zr, L.zr);
   F2 zi2 = f2_mul(L.zi, L.zi);
   F2 s = f2_add(zr2, zi2);

@@ -550,6 +550,36 @@ extern "C" int mb_model_load(const char* path, float* params) {
 
 namespace mb {
 
+int order_tiles(const uint32_t* probe, const float* feat, uint32_t nt, const float* params, uint32_t tile,
+                uint32_t grid, uint32_t split, mb_item* items, uint32_t capacity, uint32_t* n_items, uint32_t* status,
+                cudaStream_t st) {
+  if (!probe || !items || !n_items || nt == 0 || grid == 0 || (params && !feat)) return MB_EINVAL;
+  if (split == 0) split = 4;
+  if (split > 4096) split = 4096;
+  size_t bytes = a256((size_t)nt * 4) + a256(nt) + a256((size_t)nt * 4);
+  char* ws = nullptr;
+  if (cudaMallocAsync((void**)&ws, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return MB_ENOMEM;
+  }
+  float* y = (float*)ws;
+  uint8_t* qbuf = (uint8_t*)(ws + a256((size_t)nt * 4));
+  uint32_t* order = (uint32_t*)(ws + a256((size_t)nt * 4) + a256(nt));
+  int rc = MB_OK;
+  if (params) {
+    rc = mb_mlp_forward(params, feat, nt, y, st);
+  } else {
+    probe_sum_cost_kernel<<<(nt + 255) / 256, 256, 0, st>>>(probe, nt, tile, y);
+    rc = cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
+  }
+  if (rc == MB_OK) {
+    order_split_kernel<<<1, OS_T, 0, st>>>(y, nt, tile, grid, split, qbuf, order, items, capacity, n_items, status);
+    rc = cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
+  }
+  cudaFreeAsync(ws, st);
+  return rc;
+}
+
 struct LearnedLayout {
   size_t view, counter, cx, cy, probe, feat, y, items, nitems, qbuf, order, total;
 };

@@ -295,7 +295,7 @@ __device__ __forceinline__ void render_body(RenderParams P) {
     }
     block_begin(L);
 #pragma unroll
-    for (int u = 0; u < UNROLL; ++u) step<FILT, EMUL>(L, r2, thr);
+    for (int u = 0; u < UNROLL; ++u) step<FILT, EMUL>(L, r2, thr, isub_step(u));
   }
 
   __syncthreads();

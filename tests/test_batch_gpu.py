@@ -96,3 +96,33 @@ def test_batch_rejects_bad_views():
     assert e.value.code == 1
     with pytest.raises(mb.MBError):
         mb.mb_render_batch(vs[:1], [0])
+
+
+@pytest.mark.parametrize("model", ["probe_sum", "network"])
+@pytest.mark.parametrize("tile", [16, 32])
+def test_batch_learned_order(orc, model, tile):
+    """The learned longest-first queue (probe of every view, predicted costs,
+    heavy tiles split into strips) changes only the order: one-shot and graph
+    plan both equal the oracle; any network gives a valid queue."""
+    vs = [v for v in small_batch() if v.iter_max > 0]
+    params = torch.from_numpy(wl.mlp_init()).cuda() if model == "network" else None
+    outs = _outs(vs)
+    mb.mb_render_batch(vs, outs, tile=tile, learned_order=1, model=params)
+    _check(orc, vs, outs)
+    outs = _outs(vs)
+    plan = mb.BatchPlan(vs, outs, tile=tile, block=512, learned_order=1, model=params, split=2)
+    n_tiles = sum((-(-v.m // tile)) * (-(-v.n // tile)) for v in vs)
+    assert plan.info()["items"] >= n_tiles            # every tile at least once, heavy ones in strips
+    plan.launch()
+    _check(orc, vs, outs)
+    for o in outs:
+        o.fill_(-3)
+    plan.launch()
+    _check(orc, vs, outs)
+    plan.destroy()
+
+
+def test_batch_learned_order_needs_tile_16():
+    vs = small_batch()[:3]
+    with pytest.raises(mb.MBError):
+        mb.mb_render_batch(vs, _outs(vs), tile=8, learned_order=1)

@@ -20,7 +20,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_bench_json_line_contract():
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--steps", "2", "--warmup", "3", "--size", "1024",
-           "--iter-max", "2000", "--no-compare", "--no-batch", "--no-serve", "--no-precision", "--no-cycle"]
+           "--iter-max", "2000", "--no-compare", "--no-batch", "--no-serve", "--no-precision", "--no-cycle", "--no-zoom"]
     out = subprocess.run(cmd, check=True, capture_output=True, text=True, timeout=600, cwd=ROOT).stdout
     lines = [ln for ln in out.splitlines() if ln.startswith("{")]
     assert len(lines) == 1

@@ -58,3 +58,52 @@ def test_range_test_routes_the_rest_to_replay():
     sq, pr, ok = _run(np.array([2.0 ** -510, -(2.0 ** 510) * 1.5]), np.array([2.0 ** 510, 2.0 ** -510]))
     assert ok.all()
     assert sq[0] == 2.0 ** -1020 and pr[0] == 2.0 and pr[1] == -3.0
+
+
+def _positive(n, seed, e_lo, e_hi, short_every=3):
+    return np.abs(_doubles(n, seed, e_lo, e_hi, short_every))
+
+
+def _run_sub(a, b):
+    A, B = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    d = torch.empty_like(A)
+    ok = torch.empty(a.size, dtype=torch.uint8, device="cuda")
+    mb.mb_selftest_psub(A, B, d, ok)
+    torch.cuda.synchronize()
+    return d.cpu().numpy(), ok.cpu().numpy().astype(bool)
+
+
+@pytest.mark.parametrize("spread", [0, 1, 2, 40, 253])
+def test_integer_subtraction_bit_exact(spread):
+    """RN(a - b) for positive normal a, b in the squares' range [2^-126, 2^128),
+    against numpy's binary64 subtraction, wherever the kernel keeps the result;
+    exponents equal, one apart, close and far; mantissas that cancel and that tie."""
+    n = 1 << 21
+    e = 1023 - 126 + (wl.splitmix_keys(n, 91 + spread) % np.uint64(254 - spread)).astype(np.int64)
+    de = (wl.splitmix_keys(n, 92 + spread) % np.uint64(2 * spread + 1)).astype(np.int64) - spread
+    eb = np.clip(e + de, 1023 - 126, 1023 + 127)
+    a = _positive(n, 3 + spread, 1023, 1023) * np.ldexp(1.0, (e - 1023).astype(np.int32))
+    b = _positive(n, 5 + spread, 1023, 1023) * np.ldexp(1.0, (eb - 1023).astype(np.int32))
+    close = np.arange(n) % 4 == 0            # b shares a's leading bits: cancellation
+    b = np.where(close, (a.view(np.uint64) ^ (wl.splitmix_keys(n, 7) & np.uint64(0xFFFFF))).view(np.float64), b)
+    d, ok = _run_sub(a, b)
+    want = a - b
+    assert np.array_equal(d[ok].view(np.uint64), want[ok].view(np.uint64))
+    ea, eb2 = (a.view(np.uint64) >> np.uint64(52)).astype(np.int64), (b.view(np.uint64) >> np.uint64(52)).astype(np.int64)
+    far = np.abs(ea - eb2) > 31
+    assert not ok[far].any()                  # larger exponent gaps always go to the replay
+    assert ok[~far & ~close].mean() > 0.999   # and almost nothing else does
+    assert not ok[a == b].any()
+
+
+def test_integer_subtraction_edges():
+    two = np.float64(2.0)
+    a = np.array([1.0, 1.0, 1.5, two ** 127 * 1.75, two ** -126, 3.0, 1.0 + 2.0 ** -52, 1.0])
+    b = np.array([1.0, 0.5, 1.0 + 2.0 ** -52, two ** 100, two ** -126 * 1.5, 3.0 * (1 + 2.0 ** -52),
+                  1.0, 2.0 ** -31])
+    d, ok = _run_sub(a, b)
+    want = a - b
+    # kept: exponent gaps 1, 0, 27, 0 (b larger: a negative result), 31;
+    # replayed: a == b and the two one-ulp differences (their leading 32 bits cancel)
+    assert list(ok) == [False, True, True, True, True, False, False, True]
+    assert np.array_equal(d[ok].view(np.uint64), want[ok].view(np.uint64))
