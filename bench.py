@@ -733,9 +733,11 @@ def run_ours(args):
         cmp = {}
         variants = [("naive", dict(sched="naive", tile=64)), ("alternating", dict(sched="alternating", tile=64)),
                     ("fcfs_rows", dict(sched="fcfs_rows", tile=64)), ("fcfs_tiles64", dict(sched="fcfs_tiles", tile=64)),
-                    ("fcfs_tiles16", dict(sched="fcfs_tiles", tile=16)), ("learned", None), ("probe_sum", "probe")]
+                    ("fcfs_tiles16", dict(sched="fcfs_tiles", tile=16)), ("learned", None), ("probe_sum", "probe"),
+                    ("learned64", "learned64")]
+        params64 = tilemodel.default_model(tile=64, stream=stream)[0] if params is not None else None
         for name, kw in variants:
-            if kw is None and params is None:
+            if kw in (None, "learned64") and params is None:
                 continue
             tr = torch.zeros(g * 3, dtype=torch.int64, device=dev)
             a, b = E(), E()
@@ -744,6 +746,9 @@ def run_ours(args):
                 mb.mb_render_learned(v.window, v.m, v.n, v.iter_max, v.r2, out, params if kw is None else None,
                                      tile=args.tile, block=args.block, unroll=args.unroll, grid=g, trace=tr,
                                      stream=stream)
+            elif kw == "learned64":           # the learned pipeline on 64-pixel tiles (a 1/64 probe)
+                mb.mb_render_learned(v.window, v.m, v.n, v.iter_max, v.r2, out, params64, tile=64,
+                                     block=args.block, unroll=args.unroll, grid=g, trace=tr, stream=stream)
             else:
                 mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, out, block=args.block, unroll=args.unroll,
                              grid=g, trace=tr, stream=stream, **kw)
@@ -803,29 +808,57 @@ def run_ours(args):
         cache = os.path.join(ROOT, "paper_2007_00745_gb300", "_build", "autotune_cache.txt")
         os.makedirs(os.path.dirname(cache), exist_ok=True)
         best, tune_ms = mb.mb_batch_autotune(views, outs, sample_stride=8, cache_path=cache)
-        plan = mb.BatchPlan(views, outs, **best)
-        plan.launch()
-        torch.cuda.synchronize()
+        sms, per = mb.mb_device_info(best["block"])
+        g = sms * per
+        btr = torch.zeros(g * 3, dtype=torch.int64, device=dev)
+
+        def time_plan(plan, reps=2):
+            plan.launch()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(reps):
+                a, b = E(), E()
+                a.record()
+                plan.launch()
+                b.record()
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            st = trace_stats(btr.cpu().numpy().reshape(-1, 3), sms)
+            return min(ms), st
+
+        plan = mb.BatchPlan(views, outs, trace=btr, **best)
+        bm, bst = time_plan(plan)
         bi = 0
         for o in outs:
             mb.mb_sum_counts(o, total)
             torch.cuda.synchronize()
             bi += int(total.item())
-        bms = []
-        for _ in range(2):
-            a, b = E(), E()
-            a.record()
-            plan.launch()
-            b.record()
-            b.synchronize()
-            bms.append(a.elapsed_time(b))
         info = plan.info()
         plan.destroy()
-        bm = min(bms)
         line["batch"] = {"workload": "%d viewports, sides U(256..4096), widths log-U(1e-9..1e-1), " % len(views) +
                                      "iterMax log-U(256..65536), one persistent launch, CUDA graph replay",
                          "giter_s": bi / (bm * 1e-3) / 1e9, "ms": bm, "iterations": bi, "items": info["items"],
-                         "pixels": info["pixels"], "autotuned": best, "autotune_sample_ms": tune_ms}
+                         "pixels": info["pixels"], "autotuned": best, "autotune_sample_ms": tune_ms,
+                         "queue": "views by decreasing iterMax, tiles in raster order",
+                         "makespan_ms": bst["makespan_ms"], "idle_tail": bst["idle_tail"]}
+        # the same batch with the learned queue: every view probed once when the plan is built,
+        # (view, tile) items of all views longest-first by the tile-cost network, heavy tiles split
+        if best["tile"] >= 16:
+            bparams = tilemodel.default_model(tile=best["tile"], stream=stream)[0]
+            louts = [torch.empty_like(o) for o in outs]
+            t = time.perf_counter()
+            lplan = mb.BatchPlan(views, louts, trace=btr, learned_order=1, model=bparams, **best)
+            torch.cuda.synchronize()
+            build_s = time.perf_counter() - t
+            lm, lst = time_plan(lplan)
+            linfo = lplan.info()
+            lplan.destroy()
+            same = all(bool(torch.equal(x, y)) for x, y in zip(outs, louts))
+            line["batch"]["learned"] = {"giter_s": bi / (lm * 1e-3) / 1e9, "ms": lm, "items": linfo["items"],
+                                        "makespan_ms": lst["makespan_ms"], "idle_tail": lst["idle_tail"],
+                                        "plan_build_s": build_s, "same_counts": same,
+                                        "speedup_vs_default_queue": bm / lm}
+            del louts
         if not args.no_cycle:   # the same batch with exact cycle detection: time and identical counts only
             couts = [torch.empty_like(o) for o in outs]
             cplan = mb.BatchPlan(views, couts, cycle_check=1, **best)

@@ -141,7 +141,8 @@ typedef struct {
   uint32_t learned_order;    /* mb_render_batch / mb_batch_plan_create: 1 = queue the (view, tile) items of all
                                 views longest-first by predicted cost, with heavy tiles split into row strips (the
                                 order-and-split rule of mb_order_split over the batch's tiles, split divisor
-                                `split`), instead of decreasing iterMax then raster order; the costs come from a
+                                `split`, on the costs after the neighbourhood guard of mb_guard_costs within
+                                each view), instead of decreasing iterMax then raster order; the costs come from a
                                 probe of every view (8 x 8 samples per tile, tile >= 16) run once when the plan is
                                 built, and from `model` (or, when model is NULL, the probe-sum estimate).
                                 Scheduling only: the counts are unchanged.  0 = off */
@@ -400,13 +401,24 @@ int mb_order_split(const float* cost_pred, uint32_t ntiles, uint32_t tile, uint3
                    mb_item* items, uint32_t capacity, uint32_t* n_items, uint32_t* status, void* stream);
 
 /* The learned pipeline for one view: probe (its samples go straight into
- * `out`), features, network, order and split, then the FCFS render of the other
- * pixels over that list.  Same counts as mb_render.  opts->tile >= 16 (default
+ * `out`), features, network, neighbourhood guard (mb_guard_costs), order and
+ * split, then the FCFS render of the other pixels over that list.  Same counts as mb_render.  opts->tile >= 16 (default
  * 64); opts->sched is ignored; opts->trace records the final render's CTAs.
  * params == NULL is the ablation without the network: each tile's cost is
  * taken as log2(1 + (T*T/64) * sum of its probe counts) / 32. */
 int mb_render_learned(const mb_window* w, uint32_t m, uint32_t n, uint32_t iter_max, double escape_r2,
                       uint32_t* out, const float* params, const mb_opts* opt);
+
+/* Neighbourhood guard of predicted tile costs (device, tiles_x * tiles_y floats,
+ * row-major tiles of one view): guarded[t] = the largest cost_pred over the 3 x 3
+ * tiles around t that lie in the grid (NaN values are ignored; NaN only where all
+ * of them are NaN).  The learned render and learned batch queues order and split
+ * by the guarded costs: the set's interior regions are connected, so a tile whose
+ * probe missed them almost always borders tiles whose probe saw them, and the
+ * guard keeps it out of the cheap end of the queue, where one mispredicted heavy
+ * tile would set the makespan.  Not in the paper (scheduling only).  Asynchronous
+ * on `stream`; guarded must not overlap cost_pred.  Errors: MB_EINVAL, MB_ECUDA. */
+int mb_guard_costs(const float* cost_pred, uint32_t tiles_x, uint32_t tiles_y, float* guarded, void* stream);
 
 /* Save / load the network parameters (device, MB_MLP_PARAMS floats) as a small
  * binary file: 8-byte tag "MBMLP701", uint32 count, float32 values. */

@@ -36,6 +36,11 @@ order and split (integers after one FP32 quantisation):
                                                      saturates at 2^64 - 1
     s_t = smallest power of two >= ceil(c(q_t) / target), at most min(16, T / 4)
     items: for each tile in sorted order, rows [k T/s_t, (k+1) T/s_t), k < s_t
+
+neighbourhood guard (applied to y before order and split by the learned render and
+the learned batch queue; each view on its own tile grid):
+    g_t = max of y over the tiles within one tile of t (3 x 3, cut at the grid's
+          edge), NaN ignored (NaN only when all of them are NaN), in FP32
 """
 import numpy as np
 
@@ -136,6 +141,18 @@ def level_cost(q):
     """c(q) in exact integer arithmetic (uint64 on both sides: at most 2^47 * 110218)."""
     return np.array([((1 << (int(k) >> 2)) * SPLIT_M[int(k) & 3]) >> 16 for k in np.atleast_1d(q)],
                     dtype=np.uint64)
+
+
+def guard_costs(y, tiles_x, tiles_y):
+    """Neighbourhood guard: the largest y (float32) over the 3 x 3 tiles around each
+    tile of a tiles_y x tiles_x grid, ignoring NaN."""
+    a = np.asarray(y, dtype=np.float32).reshape(tiles_y, tiles_x)
+    out = np.empty_like(a)
+    for r in range(tiles_y):
+        for c in range(tiles_x):
+            block = a[max(r - 1, 0):r + 2, max(c - 1, 0):c + 2]
+            out[r, c] = np.nan if np.isnan(block).all() else np.nanmax(block)
+    return out.reshape(-1)
 
 
 def order_and_split(y, tile, grid, split=4):

@@ -279,10 +279,16 @@ def mb_order_split(cost_pred, ntiles, tile, grid, items, capacity, n_items, stat
                                      int(capacity), _ptr(n_items), _ptr(status), _stream(stream)), "mb_order_split")
 
 
+def mb_guard_costs(cost_pred, tiles_x, tiles_y, guarded, stream=None):
+    """Largest predicted cost over each tile's 3 x 3 neighbourhood (float32 device tensors)."""
+    _check(_L().lib().mb_guard_costs(_ptr(cost_pred), int(tiles_x), int(tiles_y), _ptr(guarded), _stream(stream)),
+           "mb_guard_costs")
+
+
 def mb_render_learned(window, m, n, iter_max, escape_r2, out, params, **opts):
     """The learned pipeline: probe (8 x 8 samples per tile, written into `out`), tile
     features, predicted costs (`params`: the 8769 float32 parameters on the device, or
-    None for the probe-sum order), longest-first order with splits, then the FCFS
+    None for the probe-sum order), neighbourhood guard, longest-first order with splits, then the FCFS
     render of the remaining pixels.  Options as mb_render (tile >= 16; `split` is the
     split divisor).  Binary64 only."""
     L = _L()

@@ -112,6 +112,7 @@ def _load():
     L.mb_model_train.argtypes = [vp, vp, vp, vp, vp, u32, vp, u32, u32, ctypes.c_float, vp, vp]
     L.mb_order_split.argtypes = [vp, u32, u32, u32, u32, vp, u32, vp, vp, vp]
     L.mb_render_learned.argtypes = [P(mb_window), u32, u32, u32, f64, vp, vp, P(mb_opts)]
+    L.mb_guard_costs.argtypes = [vp, u32, u32, vp, vp]
     L.mb_model_save.argtypes = [vp, ctypes.c_char_p]
     L.mb_model_load.argtypes = [ctypes.c_char_p, vp]
     L.mb_render_batch.argtypes = [P(mb_view), u32, P(mb_opts)]
@@ -137,7 +138,8 @@ def _load():
                  "mb_batch_plan_destroy", "mb_batch_autotune"):
         getattr(L, name).restype = i32
     for name in ("mb_probe", "mb_tile_features", "mb_tile_targets", "mb_mlp_forward", "mb_mlp_grad", "mb_adam_step",
-                 "mb_model_train", "mb_order_split", "mb_render_learned", "mb_model_save", "mb_model_load"):
+                 "mb_model_train", "mb_order_split", "mb_render_learned", "mb_model_save", "mb_model_load",
+                 "mb_guard_costs"):
         getattr(L, name).restype = i32
     return L
 

@@ -94,9 +94,11 @@ __global__ void batch_learned_items_kernel(const mb_item* __restrict__ in, uint3
 static int batch_learned_queue(const mb_view* views, uint32_t count, const mb_opts* opt, mb_batch_plan* P) {
   const uint32_t tile = P->tile;
   if (tile < 16) return MB_EINVAL;
-  std::vector<uint32_t> goff(count + 1, 0);
-  for (uint32_t i = 0; i < count; ++i)
-    goff[i + 1] = goff[i] + ((views[i].n + tile - 1) / tile) * ((views[i].m + tile - 1) / tile);
+  std::vector<uint32_t> goff(count + 1, 0), txs(count);
+  for (uint32_t i = 0; i < count; ++i) {
+    txs[i] = (views[i].n + tile - 1) / tile;
+    goff[i + 1] = goff[i] + txs[i] * ((views[i].m + tile - 1) / tile);
+  }
   const uint32_t nt = goff[count];
   const uint32_t split = opt->split ? (opt->split > 4096 ? 4096u : opt->split) : 4u;
   uint64_t cap64 = 2ull * nt + 4ull * split * P->grid + 1024;
@@ -106,7 +108,7 @@ static int batch_learned_queue(const mb_view* views, uint32_t count, const mb_op
   size_t o_probe = 0, o_feat = b256((size_t)nt * 64 * 4);
   size_t o_items = o_feat + (opt->model ? b256((size_t)nt * MB_MLP_FEATURES * 4) : 0);
   size_t o_n = o_items + b256((size_t)cap * sizeof(mb_item));
-  size_t o_goff = o_n + 256, total = o_goff + b256((size_t)(count + 1) * 4);
+  size_t o_goff = o_n + 256, o_tx = o_goff + b256((size_t)(count + 1) * 4), total = o_tx + b256((size_t)count * 4);
   char* tmp = nullptr;
   if (cudaMalloc((void**)&tmp, total) != cudaSuccess) {
     cudaGetLastError();
@@ -122,6 +124,9 @@ static int batch_learned_queue(const mb_view* views, uint32_t count, const mb_op
   po.block = P->block;
   po.unroll = P->unroll;
   int rc = MB_OK;
+  if (cudaMemcpy(tmp + o_goff, goff.data(), (count + 1) * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(tmp + o_tx, txs.data(), count * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = MB_ECUDA;
   for (uint32_t i = 0; i < count && rc == MB_OK; ++i) {
     const mb_view& q = views[i];
     rc = mb_probe(&q.w, q.m, q.n, q.iter_max, q.escape_r2, probe + (size_t)goff[i] * 64, nullptr, &po);
@@ -129,7 +134,9 @@ static int batch_learned_queue(const mb_view* views, uint32_t count, const mb_op
       rc = mb_tile_features(probe + (size_t)goff[i] * 64, &q.w, q.m, q.n, q.iter_max, tile,
                             feat + (size_t)goff[i] * MB_MLP_FEATURES, nullptr);
   }
-  if (rc == MB_OK) rc = order_tiles(probe, feat, nt, opt->model, tile, P->grid, split, li, cap, dn, nullptr, nullptr);
+  if (rc == MB_OK)
+    rc = order_tiles(probe, feat, nt, opt->model, tile, P->grid, split, (const uint32_t*)(tmp + o_goff),
+                     (const uint32_t*)(tmp + o_tx), count, li, cap, dn, nullptr, nullptr);
   uint32_t n = 0;
   if (rc == MB_OK && cudaMemcpy(&n, dn, 4, cudaMemcpyDeviceToHost) != cudaSuccess) rc = MB_ECUDA;
   if (rc == MB_OK && n > 0) {
@@ -137,9 +144,6 @@ static int batch_learned_queue(const mb_view* views, uint32_t count, const mb_op
       cudaGetLastError();
       rc = MB_ENOMEM;
     }
-    if (rc == MB_OK &&
-        cudaMemcpy(tmp + o_goff, goff.data(), (count + 1) * 4, cudaMemcpyHostToDevice) != cudaSuccess)
-      rc = MB_ECUDA;
     if (rc == MB_OK) {
       uint32_t nb = (uint32_t)std::min<uint64_t>((n + 255) / 256, 4096);
       batch_learned_items_kernel<<<nb, 256>>>(li, n, (const uint32_t*)(tmp + o_goff), count, P->litems);

@@ -58,12 +58,15 @@ void stats_begin(RenderParams& P, uint32_t grid, cudaStream_t st, const uint32_t
 void stats_cancel();
 
 // Longest-first item list with splits (the rule of mb_order_split) over `nt` tiles numbered
-// 0..nt-1, from their predicted costs: the network `params` on their features `feat`
+// 0..nt-1, from their predicted costs -- the network `params` on their features `feat`
 // (tiles x MB_MLP_FEATURES), or, when params is NULL, the probe-sum estimate from their
-// probe counts (tiles x 64).  Temporaries are stream-ordered allocations on `st`.
+// probe counts (tiles x 64) -- after the neighbourhood guard (mb_guard_costs) within each
+// view: view v owns tiles goff[v] .. goff[v+1]-1, tx[v] per row (device arrays; goff NULL:
+// one view, tx[0] on the host side is not read -- pass goff and tx for several views).
+// Temporaries are stream-ordered allocations on `st`.
 int order_tiles(const uint32_t* probe, const float* feat, uint32_t nt, const float* params, uint32_t tile,
-                uint32_t grid, uint32_t split, mb_item* items, uint32_t capacity, uint32_t* n_items, uint32_t* status,
-                cudaStream_t st);
+                uint32_t grid, uint32_t split, const uint32_t* goff, const uint32_t* tx, uint32_t nviews,
+                mb_item* items, uint32_t capacity, uint32_t* n_items, uint32_t* status, cudaStream_t st);
 
 inline int opt_unroll(const mb_opts* o) { return o && o->unroll ? (int)o->unroll : (int)DEFAULT_UNROLL; }
 inline uint64_t opt_deadline_ns(const mb_opts* o) { return o && o->max_seconds ? o->max_seconds * 1000000000ull : 0ull; }

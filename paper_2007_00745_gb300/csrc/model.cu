@@ -72,6 +72,35 @@ __global__ void probe_sum_cost_kernel(const uint32_t* __restrict__ probe, uint32
   y[t] = (float)(log2(1.0 + scale * (double)s) / 32.0);
 }
 
+// Neighbourhood guard of predicted costs: g[t] = the largest y over the 3 x 3
+// tiles around t within its view (NaN ignored; NaN only if all nine are NaN).
+// Views are consecutive runs of tiles: view v has tiles goff[v] .. goff[v+1]-1,
+// tx[v] per row; goff == NULL means one view of width tx1.  Interior regions of the set are connected, so a tile whose
+// probe missed them almost always borders tiles whose probe did not: with the
+// guard such tiles cannot end up at the cheap end of the longest-first queue.
+__global__ void guard_kernel(const float* __restrict__ y, uint32_t nt, const uint32_t* __restrict__ goff,
+                             const uint32_t* __restrict__ tx, uint32_t nviews, uint32_t tx1, float* __restrict__ g) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    uint32_t base = 0, w = tx1, h = nt / tx1;
+    if (goff) {
+      uint32_t lo = 0, hi = nviews;  // largest v with goff[v] <= t
+      while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) / 2;
+        if (goff[mid] <= t) lo = mid;
+        else hi = mid;
+      }
+      base = goff[lo];
+      w = tx[lo];
+      h = (goff[lo + 1] - base) / w;
+    }
+    const uint32_t r = (t - base) / w, c = (t - base) - r * w;
+    float best = y[t];
+    for (uint32_t rr = r ? r - 1 : 0; rr <= r + 1 && rr < h; ++rr)
+      for (uint32_t cc = c ? c - 1 : 0; cc <= c + 1 && cc < w; ++cc) best = fmaxf(best, y[base + rr * w + cc]);
+    g[t] = best;
+  }
+}
+
 // ---- MLP forward --------------------------------------------------------------
 
 constexpr int FWD_S = 16;  // samples per pass of a forward block (64 threads, one per hidden unit)
@@ -519,6 +548,16 @@ extern "C" int mb_order_split(const float* cost_pred, uint32_t ntiles, uint32_t 
   return rc;
 }
 
+extern "C" int mb_guard_costs(const float* cost_pred, uint32_t tiles_x, uint32_t tiles_y, float* guarded,
+                              void* stream) {
+  if (!cost_pred || !guarded || tiles_x == 0 || tiles_y == 0 || (uint64_t)tiles_x * tiles_y >= 0xFFFFFFFFull)
+    return MB_EINVAL;
+  const uint32_t nt = tiles_x * tiles_y;
+  guard_kernel<<<min((nt + 255) / 256, 4096u), 256, 0, (cudaStream_t)stream>>>(cost_pred, nt, nullptr, nullptr, 1u,
+                                                                             tiles_x, guarded);
+  return cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
+}
+
 extern "C" int mb_model_save(const float* params, const char* path) {
   if (!params || !path) return MB_EINVAL;
   std::vector<float> h(P_COUNT);
@@ -551,20 +590,22 @@ extern "C" int mb_model_load(const char* path, float* params) {
 namespace mb {
 
 int order_tiles(const uint32_t* probe, const float* feat, uint32_t nt, const float* params, uint32_t tile,
-                uint32_t grid, uint32_t split, mb_item* items, uint32_t capacity, uint32_t* n_items, uint32_t* status,
-                cudaStream_t st) {
-  if (!probe || !items || !n_items || nt == 0 || grid == 0 || (params && !feat)) return MB_EINVAL;
+                uint32_t grid, uint32_t split, const uint32_t* goff, const uint32_t* tx, uint32_t nviews,
+                mb_item* items, uint32_t capacity, uint32_t* n_items, uint32_t* status, cudaStream_t st) {
+  if (!probe || !items || !n_items || nt == 0 || grid == 0 || (params && !feat) || !goff || !tx || nviews == 0)
+    return MB_EINVAL;
   if (split == 0) split = 4;
   if (split > 4096) split = 4096;
-  size_t bytes = a256((size_t)nt * 4) + a256(nt) + a256((size_t)nt * 4);
+  size_t bytes = 2 * a256((size_t)nt * 4) + a256(nt) + a256((size_t)nt * 4);
   char* ws = nullptr;
   if (cudaMallocAsync((void**)&ws, bytes, st) != cudaSuccess) {
     cudaGetLastError();
     return MB_ENOMEM;
   }
   float* y = (float*)ws;
-  uint8_t* qbuf = (uint8_t*)(ws + a256((size_t)nt * 4));
-  uint32_t* order = (uint32_t*)(ws + a256((size_t)nt * 4) + a256(nt));
+  float* yg = (float*)(ws + a256((size_t)nt * 4));
+  uint8_t* qbuf = (uint8_t*)(ws + 2 * a256((size_t)nt * 4));
+  uint32_t* order = (uint32_t*)(ws + 2 * a256((size_t)nt * 4) + a256(nt));
   int rc = MB_OK;
   if (params) {
     rc = mb_mlp_forward(params, feat, nt, y, st);
@@ -573,7 +614,8 @@ int order_tiles(const uint32_t* probe, const float* feat, uint32_t nt, const flo
     rc = cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
   }
   if (rc == MB_OK) {
-    order_split_kernel<<<1, OS_T, 0, st>>>(y, nt, tile, grid, split, qbuf, order, items, capacity, n_items, status);
+    guard_kernel<<<min((nt + 255) / 256, 4096u), 256, 0, st>>>(y, nt, goff, tx, nviews, 0u, yg);
+    order_split_kernel<<<1, OS_T, 0, st>>>(yg, nt, tile, grid, split, qbuf, order, items, capacity, n_items, status);
     rc = cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
   }
   cudaFreeAsync(ws, st);
@@ -581,7 +623,7 @@ int order_tiles(const uint32_t* probe, const float* feat, uint32_t nt, const flo
 }
 
 struct LearnedLayout {
-  size_t view, counter, cx, cy, probe, feat, y, items, nitems, qbuf, order, total;
+  size_t view, counter, cx, cy, probe, feat, y, yg, items, nitems, qbuf, order, total;
 };
 
 static LearnedLayout learned_layout(uint32_t m, uint32_t n, uint32_t nt, uint32_t cap) {
@@ -593,7 +635,8 @@ static LearnedLayout learned_layout(uint32_t m, uint32_t n, uint32_t nt, uint32_
   L.probe = L.cy + a256((size_t)m * 8);
   L.feat = L.probe + a256((size_t)nt * 64 * 4);
   L.y = L.feat + a256((size_t)nt * NF * 4);
-  L.items = L.y + a256((size_t)nt * 4);
+  L.yg = L.y + a256((size_t)nt * 4);
+  L.items = L.yg + a256((size_t)nt * 4);
   L.nitems = L.items + a256((size_t)cap * sizeof(mb_item));
   L.qbuf = L.nitems + 256;
   L.order = L.qbuf + a256(nt);
@@ -719,7 +762,9 @@ extern "C" int mb_render_learned(const mb_window* w, uint32_t m, uint32_t n, uin
   if (rc == MB_OK) {
     uint32_t split = opt && opt->split ? opt->split : 4u;
     if (split > 4096) split = 4096;
-    order_split_kernel<<<1, OS_T, 0, st>>>((const float*)(ws + lay.y), nt, tile, grid, split, (uint8_t*)(ws + lay.qbuf),
+    guard_kernel<<<min((nt + 255) / 256, 4096u), 256, 0, st>>>((const float*)(ws + lay.y), nt, nullptr, nullptr, 1u, tx,
+                                                               (float*)(ws + lay.yg));
+    order_split_kernel<<<1, OS_T, 0, st>>>((const float*)(ws + lay.yg), nt, tile, grid, split, (uint8_t*)(ws + lay.qbuf),
                                            (uint32_t*)(ws + lay.order), (mb_item*)(ws + lay.items), cap,
                                            (uint32_t*)(ws + lay.nitems), P.status);
     rc = cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;

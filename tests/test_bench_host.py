@@ -33,13 +33,14 @@ def test_percentiles():
 
 
 def test_roofline_entry_arithmetic():
-    # 1e11 steps in 600 ms against a 0.5 T ops/s FP64 pipe: 3 x 1e11 / 0.6 = 0.5e12 -> the pipe is full
-    r = bench.roofline_entry(100_000_000_000, 600.0, 0.5e12, None)
+    # 1.2e11 steps in 600 ms against a 0.5 T ops/s FP64 pipe: 2.5 FP64-pipe additions per step
+    # on average -> 2.5 x 1.2e11 / 0.6 = 0.5e12 -> the pipe is full
+    r = bench.roofline_entry(120_000_000_000, 600.0, 0.5e12, None)
     assert abs(r["fp64_pipe_frac"] - 1.0) < 1e-12
     assert abs(r["frac"] - r["fp64_pipe_frac"]) < 1e-12
-    assert abs(r["peak"] - 0.5 * 8 / 3) < 1e-12
-    assert abs(r["achieved"] - 8e11 / 0.6 / 1e12) < 1e-12
-    assert abs(r["nominal_frac"] - 8 / 3 * r["frac"]) < 1e-12
+    assert abs(r["peak"] - 0.5 * 8 / 2.5) < 1e-12
+    assert abs(r["achieved"] - 8 * 1.2e11 / 0.6 / 1e12) < 1e-12
+    assert abs(r["nominal_frac"] - 8 / 2.5 * r["frac"]) < 1e-12
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["traffic"] is None
 
 

@@ -276,3 +276,20 @@ def test_trained_network_beats_the_probe_sum_on_held_out_views():
           % (mse_net, mse_ps, rho_net, rho_ps))
     assert mse_net < 0.9 * mse_ps
     assert rho_net > rho_ps - 1e-3
+
+
+@pytest.mark.parametrize("tx,ty", [(1, 1), (1, 7), (9, 1), (37, 23), (256, 256)])
+def test_guard_parity(tx, ty):
+    """mb_guard_costs equals the oracle's neighbourhood guard exactly (a max of
+    float32 values), with NaN, zero and negative predictions mixed in."""
+    y = wl.random_costs(tx * ty, seed=wl.SEED + tx * 131 + ty)
+    y[::11] = np.nan
+    y[::17] = 0.0
+    yd = torch.from_numpy(y).cuda()
+    g = torch.empty_like(yd)
+    mb.mb_guard_costs(yd, tx, ty, g)
+    torch.cuda.synchronize()
+    want = om.guard_costs(y, tx, ty)
+    got = g.cpu().numpy()
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    assert np.array_equal(got[~np.isnan(got)], want[~np.isnan(want)])

@@ -138,3 +138,31 @@ def test_unusable_predictions_fall_back_to_plain_fcfs():
     items = M.order_and_split(y, 64, 1000, 4)
     assert list(dict.fromkeys(it[0] for it in items)) == [2, 0, 1]
     assert items[-1] == (1, 0, 64)
+
+
+def test_guard_hand_example():
+    """3 x 4 grid: each output is the maximum over the cells within one step
+    (worked by hand), NaN ignored, edges cut."""
+    nan = float("nan")
+    y = [0.1, 0.0, 0.0, 0.0,
+         0.0, 0.0, 0.0, 0.5,
+         nan, nan, 0.0, 0.0]
+    want = [0.1, 0.1, 0.5, 0.5,
+            0.1, 0.1, 0.5, 0.5,
+            0.0, 0.0, 0.5, 0.5]
+    assert M.guard_costs(y, 4, 3).tolist() == pytest.approx(want)
+    # all-NaN neighbourhoods stay NaN (and map to level 0: plain FCFS order)
+    g = M.guard_costs([nan] * 4, 2, 2)
+    assert np.isnan(g).all() and (M.cost_level(g) == 0).all()
+
+
+def test_guard_properties():
+    rng = np.random.default_rng(5)
+    y = rng.random((7, 9)).astype(np.float32)
+    g = M.guard_costs(y.reshape(-1), 9, 7).reshape(7, 9)
+    assert (g >= y).all()                                   # never lowers a cost
+    assert set(g.reshape(-1).tolist()) <= set(y.reshape(-1).tolist())   # takes values of y only
+    i, j = np.unravel_index(np.argmax(y), y.shape)
+    assert (g[max(i - 1, 0):i + 2, max(j - 1, 0):j + 2] == y.max()).all()   # the peak spreads one tile
+    one = M.guard_costs(np.array([0.3], np.float32), 1, 1)
+    assert one.tolist() == pytest.approx([0.3])
