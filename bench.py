@@ -892,6 +892,14 @@ def run_ours(args):
                                "note": "offered_giter_s = rate x mean iterations per request; below the render "
                                        "rate the arrivals bound the delivered Giter/s, above it queueing sets p99",
                                "rates": runs}
+        # the same draw with the learned tile order in every request (probe, network, guard, rank),
+        # at the sweep's two lowest rates and its highest
+        if params is not None:
+            rates = sorted(float(r) for r in args.serve_sweep.split(","))
+            pick = sorted(set(rates[:2] + rates[-1:]))
+            line["serve_sweep"]["learned_order"] = [
+                run_serve(mb, wl, torch, r, args.serve_sweep_count, views=sweep_views, learned_order=1, model=params,
+                          tile=args.tile) for r in pick]
 
     if not args.no_zoom:
         z = wl.ZOOM_3

@@ -138,7 +138,7 @@ typedef struct {
                                 paper.  Honoured by mb_render, mb_render_batch, mb_batch_plan_create and
                                 mb_serve_create (binary64 only, not with fp64_products); the other entry points
                                 return MB_EINVAL for it; 0 = off */
-  uint32_t learned_order;    /* mb_render_batch / mb_batch_plan_create: 1 = queue the (view, tile) items of all
+  uint32_t learned_order;    /* mb_render_batch / mb_batch_plan_create (mb_serve_create: see there): 1 = queue the (view, tile) items of all
                                 views longest-first by predicted cost, with heavy tiles split into row strips (the
                                 order-and-split rule of mb_order_split over the batch's tiles, split divisor
                                 `split`, on the costs after the neighbourhood guard of mb_guard_costs within
@@ -303,7 +303,13 @@ typedef struct {
 typedef struct mb_server mb_server;
 
 /* opts: tile (default 32), block (512), unroll (8), grid, round_tiles, precision and
- * cycle_check (as for mb_render, applied to every request); other fields ignored.
+ * cycle_check (as for mb_render, applied to every request), learned_order and
+ * model (not in the paper: each admitted request is probed once, 8 x 8 samples
+ * per tile written into its counts, its tiles' costs predicted by `model` or the
+ * probe-sum estimate and guarded as in mb_guard_costs, and its tiles handed to
+ * the rounds longest-first instead of in raster order; tile >= 16; the probe
+ * counts, features and ranking are charged to the budget with the request; the
+ * model must stay valid until mb_serve_destroy); other fields ignored.
  * queue_limit 0 = 1024.  The budget is a charge, not a reservation: if the device
  * cannot allocate an admitted request's memory (a budget above the free device
  * memory), every pending request fails with MB_ECUDA and later calls return it. */

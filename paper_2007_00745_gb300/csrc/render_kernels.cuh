@@ -33,6 +33,7 @@ struct ViewDesc {
   EscThr thr;
   uint32_t m, n, iter_max, tiles_x, tiles_y;
   uint32_t pad_;
+  const uint32_t* order;  // batched items only: if set, item tile k stands for tile order[k] of the view
 };
 
 // Work item of the batched list: rows [row0, row0+rows) of tile `tile` of view `view`.
@@ -205,6 +206,7 @@ __device__ __forceinline__ bool decode(const RenderParams& P, uint32_t it, uint3
     return false;
   }
   const ViewDesc& V = P.views[v];
+  if (KIND == KIND_BATCH && V.order) t = V.order[t];  // a served request's learned tile order
   uint32_t ty = t / V.tiles_x, tx = t - ty * V.tiles_x;
   uint32_t lr = r0 + (pix >> P.log2_tile), lc = pix & ((1u << P.log2_tile) - 1u);
   row = (ty << P.log2_tile) + lr;

@@ -9,6 +9,11 @@
 // When a round's event fires, its tiles are done; a request whose tiles are all
 // done is complete.  All per-request state (view descriptor, Cx / Cy, counts)
 // stays on the device; the host keeps only tile counters and timestamps.
+// With opts->learned_order each admitted request is probed once (8 x 8
+// samples per tile, written into its counts and skipped by the rounds), its
+// tiles' costs are predicted (network or probe-sum estimate), guarded and
+// ranked longest-first on the device; rounds then hand out its tiles by rank,
+// and the render kernel reads the tile through that permutation.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -45,7 +50,7 @@ struct Req {
   uint32_t slot = 0;
   size_t bytes = 0;
   char* dmem = nullptr;  // counts then Cx, Cy
-  uint32_t tiles = 0, next_tile = 0, done_tiles = 0;
+  uint32_t tiles = 0, tiles_x = 0, next_tile = 0, done_tiles = 0;
   uint64_t submit_ns = 0, admit_ns = 0, start_ns = 0, done_ns = 0;
   bool released = false;
 };
@@ -88,14 +93,88 @@ struct mb_server {
   cudaEvent_t setup_ev = nullptr;
   cudaMemPool_t pool = nullptr;  // the server's own pool: freed request memory stays reserved for the next ones
   mb::Round rounds[mb::SERVE_STREAMS];
-  mb::RenderFn fn_filt = nullptr, fn_exact = nullptr;
+  mb::RenderFn fn_filt = nullptr, fn_exact = nullptr, fn_probe_filt = nullptr, fn_probe_exact = nullptr;
+  bool learned = false;         // opts->learned_order: rank each request's tiles by predicted cost
+  const float* model = nullptr;  // the tile-cost network (may be null: probe-sum estimate)
+  uint32_t* d_probe_counter = nullptr;
   mb_serve_counters ctr{};
 };
 
 namespace mb {
 
-static size_t req_bytes(const mb_request& r) {
-  return s256((size_t)r.m * r.n * 4) + s256((size_t)(r.m + r.n) * 8);
+// Device memory of a request: counts, Cx / Cy, and for a learned order the probe
+// counts, features, ranked items, permutation and the view table of its ranking.
+struct ReqLayout {
+  size_t cx, probe, feat, items, perm, meta, total;
+};
+
+static ReqLayout req_layout(const mb_request& r, uint32_t tile, bool learned, bool model) {
+  ReqLayout L;
+  const size_t nt = (size_t)((r.n + tile - 1) / tile) * ((r.m + tile - 1) / tile);
+  L.cx = s256((size_t)r.m * r.n * 4);
+  L.probe = L.cx + s256((size_t)(r.m + r.n) * 8);
+  L.feat = L.probe + (learned ? s256(nt * 64 * 4) : 0);
+  L.items = L.feat + (learned && model ? s256(nt * MB_MLP_FEATURES * 4) : 0);
+  L.perm = L.items + (learned ? s256(nt * sizeof(mb_item)) : 0);
+  L.meta = L.perm + (learned ? s256(nt * 4) : 0);
+  L.total = L.meta + (learned ? 256 : 0);
+  return L;
+}
+
+// meta = {goff = (0, nt), tx = (tiles_x), n_items}: the one-view table order_tiles reads
+__global__ void serve_meta_kernel(uint32_t* meta, uint32_t nt, uint32_t tiles_x) {
+  meta[0] = 0u;
+  meta[1] = nt;
+  meta[2] = tiles_x;
+  meta[3] = 0u;
+}
+
+// perm[k] = tile of rank k; the identity if the ranking did not produce one item per tile
+__global__ void serve_perm_kernel(const mb_item* __restrict__ items, uint32_t nt, const uint32_t* __restrict__ n_items,
+                                  uint32_t* __restrict__ perm) {
+  const bool ok = *n_items == nt;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nt; k += gridDim.x * blockDim.x)
+    perm[k] = ok ? items[k].tile : k;
+}
+
+// Probe, predict, guard and rank one admitted request's tiles on the setup stream.
+static int learn_order_locked(mb_server* S, Req& R) {
+  ReqLayout L = req_layout(R.rq, S->tile, true, S->model != nullptr);
+  const uint32_t nt = R.tiles;
+  uint32_t* probe = (uint32_t*)(R.dmem + L.probe);
+  float* feat = S->model ? (float*)(R.dmem + L.feat) : nullptr;
+  mb_item* items = (mb_item*)(R.dmem + L.items);
+  uint32_t* meta = (uint32_t*)(R.dmem + L.meta);
+  uint32_t log2_tile = 0;
+  while ((1u << log2_tile) < S->tile) ++log2_tile;
+  if (cudaMemsetAsync(S->d_probe_counter, 0, 4, S->setup) != cudaSuccess) return MB_ECUDA;
+  RenderParams PP;
+  std::memset(&PP, 0, sizeof PP);
+  PP.views = S->d_views + R.slot;
+  PP.log2_tile = log2_tile;
+  PP.counter = S->d_probe_counter;
+  PP.probe_out = probe;
+  PP.n_items = nt;
+  RenderFn fp = filter_ok(R.rq.escape_r2) ? S->fn_probe_filt : S->fn_probe_exact;
+  int rc = launch_render(fp, PP, S->grid, S->block, S->setup);
+  if (rc) return rc;
+  serve_meta_kernel<<<1, 1, 0, S->setup>>>(meta, nt, R.tiles_x);
+  if (cudaGetLastError() != cudaSuccess) return MB_ECUDA;
+  if (feat) {
+    rc = mb_tile_features(probe, &R.rq.w, R.rq.m, R.rq.n, R.rq.iter_max, S->tile, feat, S->setup);
+    if (rc) return rc;
+  }
+  // one rank per tile: a work list without splits (one worker, split divisor 1)
+  rc = order_tiles(probe, feat, nt, S->model, S->tile, 1u, 1u, meta, meta + 2, 1u, items, nt, meta + 3, nullptr,
+                   S->setup);
+  if (rc) return rc;
+  serve_perm_kernel<<<(nt + 255) / 256 < 1024 ? (nt + 255) / 256 : 1024, 256, 0, S->setup>>>(
+      items, nt, meta + 3, (uint32_t*)(R.dmem + L.perm));
+  return cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
+}
+
+static size_t req_bytes(const mb_server* S, const mb_request& r) {
+  return req_layout(r, S->tile, S->learned, S->model != nullptr).total;
 }
 
 // Admit queued requests that fit (caller holds the lock).  Device work is
@@ -130,10 +209,15 @@ static int admit_locked(mb_server* S) {
     V.iter_max = R.rq.iter_max;
     V.tiles_x = (R.rq.n + S->tile - 1) / S->tile;
     V.tiles_y = (R.rq.m + S->tile - 1) / S->tile;
+    if (S->learned) V.order = (const uint32_t*)(R.dmem + req_layout(R.rq, S->tile, true, S->model != nullptr).perm);
     if (cudaMemcpyAsync(S->d_views + R.slot, &V, sizeof V, cudaMemcpyHostToDevice, S->setup) != cudaSuccess)
       return MB_ECUDA;
     pixel_map_kernel<<<dim3(16, 1), 256, 0, S->setup>>>(S->d_views + R.slot, nullptr);
     if (cudaGetLastError() != cudaSuccess) return MB_ECUDA;
+    if (S->learned) {
+      int rc = learn_order_locked(S, R);
+      if (rc) return rc;
+    }
     R.state = RQ_LIVE;
     R.admit_ns = now_ns();
     S->live.push_back(R.id);
@@ -186,6 +270,7 @@ static int launch_round_locked(mb_server* S, int k, bool* launched) {
   P.log2_tile = 0;
   while ((1u << P.log2_tile) < S->tile) ++P.log2_tile;
   P.counter = Rd.d_counter;
+  P.skip_probe = S->learned ? 1u : 0u;  // the probe already wrote its samples
   int rc = launch_render(S->filt_all ? S->fn_filt : S->fn_exact, P, S->grid, S->block, st);
   if (rc) return rc;
   if (cudaEventRecord(Rd.ev, st) != cudaSuccess) return MB_ECUDA;
@@ -292,6 +377,7 @@ extern "C" int mb_serve_create(size_t mem_budget_bytes, uint32_t queue_limit, co
   if (!o.unroll) o.unroll = 8;
   int rc = check_opts(&o, &log2_tile, ALLOW_CYCLE | ALLOW_PRECISION);
   if (rc) return rc;
+  if (o.learned_order && o.tile < 16) return MB_EINVAL;  // the probe takes 8 x 8 samples per tile
   mb_server* S = new mb_server();
   S->budget = mem_budget_bytes;
   S->queue_limit = queue_limit ? queue_limit : 1024;
@@ -308,6 +394,12 @@ extern "C" int mb_serve_create(size_t mem_budget_bytes, uint32_t queue_limit, co
                                 : render_fn(KIND_BATCH, S_FCFS, false, (int)S->unroll);
   }
   S->grid = o.grid ? o.grid : default_grid(S->fn_filt, S->block);
+  if (o.learned_order) {
+    S->learned = true;
+    S->model = o.model;
+    S->fn_probe_filt = render_fn(KIND_PROBE, S_FCFS, true, (int)S->unroll);
+    S->fn_probe_exact = render_fn(KIND_PROBE, S_FCFS, false, (int)S->unroll);
+  }
   S->round_tiles = o.round_tiles ? o.round_tiles : 16 * S->grid;
   cudaMemPoolProps props;
   std::memset(&props, 0, sizeof props);
@@ -321,7 +413,8 @@ extern "C" int mb_serve_create(size_t mem_budget_bytes, uint32_t queue_limit, co
             cudaMalloc((void**)&S->d_views, SERVE_SLOTS * sizeof(ViewDesc)) == cudaSuccess &&
             cudaMallocHost((void**)&S->h_view_stage, SERVE_SLOTS * sizeof(ViewDesc)) == cudaSuccess &&
             cudaStreamCreateWithFlags(&S->setup, cudaStreamNonBlocking) == cudaSuccess &&
-            cudaEventCreateWithFlags(&S->setup_ev, cudaEventDisableTiming) == cudaSuccess;
+            cudaEventCreateWithFlags(&S->setup_ev, cudaEventDisableTiming) == cudaSuccess &&
+            cudaMalloc((void**)&S->d_probe_counter, 256) == cudaSuccess;
   for (int k = 0; k < SERVE_STREAMS && ok; ++k) {
     Round& Rd = S->rounds[k];
     ok = cudaStreamCreateWithFlags(&S->streams[k], cudaStreamNonBlocking) == cudaSuccess &&
@@ -351,7 +444,7 @@ extern "C" int mb_serve_submit(mb_server* S, const mb_request* rq, uint64_t* id)
   std::lock_guard<std::mutex> g(S->mu);
   if (S->failed != MB_OK) return S->failed;
   if (S->stop) return MB_EBUSY;
-  size_t bytes = req_bytes(*rq);
+  size_t bytes = req_bytes(S, *rq);
   if (bytes > S->budget) {
     S->ctr.rejected++;
     return MB_ENOMEM;
@@ -366,6 +459,7 @@ extern "C" int mb_serve_submit(mb_server* S, const mb_request* rq, uint64_t* id)
   R.rq = *rq;
   R.bytes = bytes;
   R.tiles = tiles_x * tiles_y;
+  R.tiles_x = tiles_x;
   R.submit_ns = now_ns();
   S->reqs[R.id] = R;
   S->queue.push_back(R.id);
@@ -506,6 +600,7 @@ extern "C" int mb_serve_destroy(mb_server* S) {
   if (S->setup_ev) cudaEventDestroy(S->setup_ev);
   if (S->setup) cudaStreamDestroy(S->setup);
   if (S->d_views) cudaFree(S->d_views);
+  if (S->d_probe_counter) cudaFree(S->d_probe_counter);
   if (S->h_view_stage) cudaFreeHost(S->h_view_stage);
   if (S->pool) cudaMemPoolDestroy(S->pool);
   delete S;

@@ -136,3 +136,34 @@ def test_injected_failure_reaches_waiters():
     assert e.value.code == mb.MB_ECUDA
     srv.release(a)
     srv.destroy()
+
+
+@pytest.mark.parametrize("model", ["probe_sum", "network"])
+def test_learned_order_serves_the_same_counts(orc, model):
+    """With the learned order each request is probed, its tiles ranked by
+    predicted cost and handed out by rank: the counts equal the lone render
+    (and the oracle), whatever the network; ragged and tiny views included."""
+    params = torch.from_numpy(wl.mlp_init()).cuda() if model == "network" else None
+    views = wl.batch_views(count=24, seed=wl.SEED + 93, side_range=(20, 500), iter_range=(64, 6000))
+    views.append(wl.View((-2.0, 1.0, -1.0, 1.0), 1, 1, 50))
+    srv = mb.Server(budget_bytes=1 << 30, tile=32, learned_order=1, model=params)
+    ids = [srv.submit(v) for v in views]
+    for rid, v in zip(ids, views):
+        rc, _ = srv.wait(rid, 120000)
+        assert rc == 0, rc
+        got = _fetch(srv, rid, v)
+        alone = torch.empty_like(got)
+        mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, alone)
+        torch.cuda.synchronize()
+        assert torch.equal(got, alone)
+        srv.release(rid)
+    v = views[5]
+    rid = srv.submit(v)
+    assert srv.wait(rid)[0] == 0
+    got = _fetch(srv, rid, v).cpu().numpy().view(np.uint32).reshape(v.m, v.n)
+    assert np.array_equal(got, orc.render(v.window, v.m, v.n, v.iter_max, v.r2))
+    srv.release(rid)
+    assert srv.counters()["bytes_in_use"] == 0
+    srv.destroy()
+    with pytest.raises(mb.MBError):
+        mb.Server(budget_bytes=1 << 20, tile=8, learned_order=1)     # the probe needs tiles of 16 or more
