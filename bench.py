@@ -49,7 +49,7 @@ FP64_PIPE_OPS_PER_ITER = 2.5
 # profiles/render_kernel_list_8192x8192_it1000.md (dram read + write per launch
 # / pixels; traffic does not depend on iterMax, so it scales by pixel count);
 # used only while the kernel sources still hash to src_sha1, else null.
-NCU_RENDER = {"src_sha1": "fe7236dd453478a4b67669e03d573d6aba74c31f", "dram_bytes_per_pixel": 3.85}
+NCU_RENDER = {"src_sha1": "33d84c29cdf0a2d3dd5ce118fefe6dd268caffcf", "dram_bytes_per_pixel": 3.868}
 KERNEL_SOURCES = ("escape_core.cuh", "escape_lowp.cuh", "render_kernels.cuh")
 
 
@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--tile", type=int, default=32)
     p.add_argument("--block", type=int, default=512)
     p.add_argument("--unroll", type=int, default=8)
+    p.add_argument("--min-strips", type=int, default=4,
+                   help="learned order: cut every tile into at least this many row strips (power of two)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-peak", action="store_true", help="skip the FP64 microbenchmark (profiling runs)")
     p.add_argument("--no-e2e", action="store_true")
@@ -107,9 +109,10 @@ def bench_view(args):
 
 def bench_config(args, v, ws):
     """The workload of both arms (ours and --impl reference): the same dict in both JSON lines."""
-    return {"workload": "%dx%d re[-2,1] im[-1.5,1.5] iterMax %d R2 4, %s (tile %d, block %d, unroll %d)"
+    return {"workload": "%dx%d re[-2,1] im[-1.5,1.5] iterMax %d R2 4, %s (tile %d%s, block %d, unroll %d)"
                         % (v.m, v.n, v.iter_max, "learned FCFS" if args.sched == "learned" else args.sched,
-                           args.tile, args.block, args.unroll),
+                           args.tile, ", %d strips per tile at least" % args.min_strips
+                           if args.sched == "learned" else "", args.block, args.unroll),
             "l2": "counts %.0f MB per step %s 129 MB L2 (compute-bound)"
                   % (v.m * v.n * 4 / 1e6, ">" if v.m * v.n * 4 > 129e6 else "<="),
             "parallelism": ("one image sharded over %d GPUs: raster tile chunks dealt first come first served "
@@ -590,6 +593,7 @@ def run_ours(args):
     total = torch.zeros(1, dtype=torch.int64, device=dev)
     learned = args.sched == "learned"
     ropts = dict(tile=args.tile, block=args.block, unroll=args.unroll, stream=stream)
+    lopts = dict(ropts, min_strips=args.min_strips)
 
     peak = float("nan")
     if not args.no_peak:
@@ -604,7 +608,7 @@ def run_ours(args):
 
     def step(events=None):
         if learned:
-            mb.mb_render_learned(v.window, v.m, v.n, v.iter_max, v.r2, out, params, events=events, **ropts)
+            mb.mb_render_learned(v.window, v.m, v.n, v.iter_max, v.r2, out, params, events=events, **lopts)
         else:
             mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, out, sched=args.sched, events=events, **ropts)
 
@@ -690,7 +694,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             a.record(stream)
             if learned:
-                mb.mb_render_learned(v.window, v.m, v.n, v.iter_max, v.r2, host, params, **ropts)
+                mb.mb_render_learned(v.window, v.m, v.n, v.iter_max, v.r2, host, params, **lopts)
             else:
                 mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, host, sched=args.sched, **ropts)
             b.record(stream)
@@ -745,10 +749,11 @@ def run_ours(args):
             if kw is None or kw == "probe":   # learned order, or its ablation ordered by the probe sum
                 mb.mb_render_learned(v.window, v.m, v.n, v.iter_max, v.r2, out, params if kw is None else None,
                                      tile=args.tile, block=args.block, unroll=args.unroll, grid=g, trace=tr,
-                                     stream=stream)
-            elif kw == "learned64":           # the learned pipeline on 64-pixel tiles (a 1/64 probe)
+                                     min_strips=args.min_strips, stream=stream)
+            elif kw == "learned64":           # the learned pipeline on 64-pixel tiles (a 1/64 probe), 16 strips
                 mb.mb_render_learned(v.window, v.m, v.n, v.iter_max, v.r2, out, params64, tile=64,
-                                     block=args.block, unroll=args.unroll, grid=g, trace=tr, stream=stream)
+                                     block=args.block, unroll=args.unroll, grid=g, trace=tr, min_strips=16,
+                                     stream=stream)
             else:
                 mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, out, block=args.block, unroll=args.unroll,
                              grid=g, trace=tr, stream=stream, **kw)

@@ -147,6 +147,11 @@ typedef struct {
                                 built, and from `model` (or, when model is NULL, the probe-sum estimate).
                                 Scheduling only: the counts are unchanged.  0 = off */
   const float* model;        /* device, MB_MLP_PARAMS floats: the tile-cost network for learned_order; may be NULL */
+  uint32_t min_strips;       /* mb_render_learned and learned batch queues: cut every tile into at least this many
+                                row strips (a power of two <= 16 and <= tile; 0 = 1), so that the queue's items
+                                are small even where the prediction says cheap -- the order is made per tile
+                                (the probe takes 64 of each tile's pixels) while the items, and with them the
+                                tail of the render, are as fine as smaller tiles; MB_EINVAL otherwise */
 } mb_opts;
 
 /* Library version string (not in the paper). */

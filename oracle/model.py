@@ -34,7 +34,8 @@ order and split (integers after one FP32 quantisation):
     target = max(1, (sum_t c(q_t)) // (S G))        G = number of CTAs, S the split
                                                      divisor (default 4); the sum
                                                      saturates at 2^64 - 1
-    s_t = smallest power of two >= ceil(c(q_t) / target), at most min(16, T / 4)
+    s_t = smallest power of two >= max(ceil(c(q_t) / target), s_min), at most
+          max(s_min, min(16, T / 4));  s_min = min_strips (a power of two, default 1)
     items: for each tile in sorted order, rows [k T/s_t, (k+1) T/s_t), k < s_t
 
 neighbourhood guard (applied to y before order and split by the learned render and
@@ -155,7 +156,7 @@ def guard_costs(y, tiles_x, tiles_y):
     return out.reshape(-1)
 
 
-def order_and_split(y, tile, grid, split=4):
+def order_and_split(y, tile, grid, split=4, min_strips=1):
     """Item list [(tile, row0, rows)] for predicted costs y (one per tile)."""
     q = cost_level(y)
     order = np.argsort(-q, kind="stable")
@@ -166,7 +167,7 @@ def order_and_split(y, tile, grid, split=4):
     items = []
     for t in order:
         need = -(-c[t] // target)
-        s = 1
+        s = min_strips
         while s < need and s < smax:
             s *= 2
         rows = tile // s

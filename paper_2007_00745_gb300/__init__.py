@@ -59,7 +59,7 @@ def _stream(stream):
 def _opts(sched="fcfs_tiles", tile=0, grid=0, block=0, unroll=0, stream=None, items=None, n_items=0,
           tile_totals=None, trace=None, trace_len=0, status=None, workspace=None, workspace_bytes=0,
           events=None, fp64_products=0, max_seconds=None, split=0, round_tiles=0, precision="fp64",
-          cycle_check=0, learned_order=0, model=None):
+          cycle_check=0, learned_order=0, model=None, min_strips=0):
     L = _L()
     o = L.mb_opts()
     o.sched = SCHEDS[sched] if isinstance(sched, str) else int(sched)
@@ -80,6 +80,7 @@ def _opts(sched="fcfs_tiles", tile=0, grid=0, block=0, unroll=0, stream=None, it
     o.cycle_check = int(cycle_check)
     o.learned_order = int(learned_order)
     o.model = _ptr(model)
+    o.min_strips = int(min_strips)
     if events is not None:   # (start, stop) torch.cuda.Event pair recorded around the main render kernel
         handles = []
         for ev in events:

@@ -34,7 +34,7 @@ class mb_opts(ctypes.Structure):
                 ("stream", vp), ("items", vp), ("n_items", u32), ("tile_totals", vp), ("trace", vp), ("trace_len", u32),
                 ("status", vp), ("workspace", vp), ("workspace_bytes", sz), ("split", u32), ("round_tiles", u32), ("max_seconds", u32), ("fp64_products", u32),
                 ("ev_start", vp), ("ev_stop", vp), ("precision", u32),
-                ("cycle_check", u32), ("learned_order", u32), ("model", vp)]
+                ("cycle_check", u32), ("learned_order", u32), ("model", vp), ("min_strips", u32)]
 
 
 class mb_view(ctypes.Structure):

@@ -83,7 +83,8 @@ __global__ void selftest_wait_kernel(RenderParams P, uint32_t* got) {
   __syncthreads();
   if ((threadIdx.x & 31) == 0) {
     uint32_t item = 0, off = 0;
-    uint32_t n = claim<KIND_RASTER, S_FCFS>(P, &s_word, &s_taken, 32u, item, off);
+    ItemWords iw{0u, 0u, 0u};
+    uint32_t n = claim<KIND_RASTER, S_FCFS>(P, &s_word, &s_taken, 32u, P.n_items, item, off, iw);
     got[blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)] = n;
   }
 }

@@ -93,7 +93,8 @@ __global__ void batch_learned_items_kernel(const mb_item* __restrict__ in, uint3
 // queue in place when the list would not fit its capacity.
 static int batch_learned_queue(const mb_view* views, uint32_t count, const mb_opts* opt, mb_batch_plan* P) {
   const uint32_t tile = P->tile;
-  if (tile < 16) return MB_EINVAL;
+  if (tile < 16 || !min_strips_ok(opt, tile)) return MB_EINVAL;
+  const uint32_t smin = opt_min_strips(opt, tile);
   std::vector<uint32_t> goff(count + 1, 0), txs(count);
   for (uint32_t i = 0; i < count; ++i) {
     txs[i] = (views[i].n + tile - 1) / tile;
@@ -101,7 +102,7 @@ static int batch_learned_queue(const mb_view* views, uint32_t count, const mb_op
   }
   const uint32_t nt = goff[count];
   const uint32_t split = opt->split ? (opt->split > 4096 ? 4096u : opt->split) : 4u;
-  uint64_t cap64 = 2ull * nt + 4ull * split * P->grid + 1024;
+  uint64_t cap64 = (smin + 1ull) * nt + 4ull * split * P->grid + 1024;
   if (cap64 > 16ull * nt) cap64 = 16ull * nt;
   if (cap64 >= 0xFFFFFFF0ull) return MB_EINVAL;
   const uint32_t cap = (uint32_t)cap64;
@@ -135,7 +136,7 @@ static int batch_learned_queue(const mb_view* views, uint32_t count, const mb_op
                             feat + (size_t)goff[i] * MB_MLP_FEATURES, nullptr);
   }
   if (rc == MB_OK)
-    rc = order_tiles(probe, feat, nt, opt->model, tile, P->grid, split, (const uint32_t*)(tmp + o_goff),
+    rc = order_tiles(probe, feat, nt, opt->model, tile, P->grid, split, smin, (const uint32_t*)(tmp + o_goff),
                      (const uint32_t*)(tmp + o_tx), count, li, cap, dn, nullptr, nullptr);
   uint32_t n = 0;
   if (rc == MB_OK && cudaMemcpy(&n, dn, 4, cudaMemcpyDeviceToHost) != cudaSuccess) rc = MB_ECUDA;

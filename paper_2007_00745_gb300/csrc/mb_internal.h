@@ -57,7 +57,8 @@ int resident_ctas(const void* fn, int block);
 void stats_begin(RenderParams& P, uint32_t grid, cudaStream_t st, const uint32_t* counts, uint64_t npix);
 void stats_cancel();
 
-// Longest-first item list with splits (the rule of mb_order_split) over `nt` tiles numbered
+// Longest-first item list with splits (the rule of mb_order_split, every tile cut into at
+// least min_strips strips) over `nt` tiles numbered
 // 0..nt-1, from their predicted costs -- the network `params` on their features `feat`
 // (tiles x MB_MLP_FEATURES), or, when params is NULL, the probe-sum estimate from their
 // probe counts (tiles x 64) -- after the neighbourhood guard (mb_guard_costs) within each
@@ -65,8 +66,17 @@ void stats_cancel();
 // one view, tx[0] on the host side is not read -- pass goff and tx for several views).
 // Temporaries are stream-ordered allocations on `st`.
 int order_tiles(const uint32_t* probe, const float* feat, uint32_t nt, const float* params, uint32_t tile,
-                uint32_t grid, uint32_t split, const uint32_t* goff, const uint32_t* tx, uint32_t nviews,
-                mb_item* items, uint32_t capacity, uint32_t* n_items, uint32_t* status, cudaStream_t st);
+                uint32_t grid, uint32_t split, uint32_t min_strips, const uint32_t* goff, const uint32_t* tx,
+                uint32_t nviews, mb_item* items, uint32_t capacity, uint32_t* n_items, uint32_t* status,
+                cudaStream_t st);
+
+// Smallest number of strips a tile is cut into by the learned order (mb_opts.min_strips):
+// 0 -> 1; callers validate it with min_strips_ok().
+inline uint32_t opt_min_strips(const mb_opts* o, uint32_t) { return o && o->min_strips ? o->min_strips : 1u; }
+inline bool min_strips_ok(const mb_opts* o, uint32_t tile) {
+  uint32_t s = o ? o->min_strips : 0u;
+  return s == 0 || ((s & (s - 1)) == 0 && s <= 16 && s <= tile);
+}
 
 inline int opt_unroll(const mb_opts* o) { return o && o->unroll ? (int)o->unroll : (int)DEFAULT_UNROLL; }
 inline uint64_t opt_deadline_ns(const mb_opts* o) { return o && o->max_seconds ? o->max_seconds * 1000000000ull : 0ull; }

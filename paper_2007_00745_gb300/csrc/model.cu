@@ -314,7 +314,8 @@ __device__ __forceinline__ unsigned long long sat_add(unsigned long long a, unsi
 }
 
 __global__ void __launch_bounds__(OS_T) order_split_kernel(const float* __restrict__ y, uint32_t ntiles, uint32_t tile,
-                                                           uint32_t grid, uint32_t split, uint8_t* __restrict__ qbuf,
+                                                           uint32_t grid, uint32_t split, uint32_t smin,
+                                                           uint8_t* __restrict__ qbuf,
                                                            uint32_t* __restrict__ order, mb_item* __restrict__ items,
                                                            uint32_t capacity, uint32_t* __restrict__ n_items,
                                                            uint32_t* __restrict__ status) {
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(OS_T) order_split_kernel(const float* __restri
   for (uint32_t r = lo; r < hi; ++r) {
     unsigned long long c = level_cost(qbuf[order[r]]);
     unsigned long long need = (c + target - 1) / target;
-    uint32_t s = 1;
+    uint32_t s = smin;
     while (s < need && s < smax) s *= 2;
     mine += s;
   }
@@ -405,7 +406,7 @@ __global__ void __launch_bounds__(OS_T) order_split_kernel(const float* __restri
     uint32_t tt = order[r];
     unsigned long long c = level_cost(qbuf[tt]);
     unsigned long long need = (c + target - 1) / target;
-    uint32_t s = 1;
+    uint32_t s = smin;
     while (s < need && s < smax) s *= 2;
     uint32_t rows = tile / s;
     for (uint32_t k = 0; k < s; ++k, ++pos) {
@@ -541,7 +542,8 @@ extern "C" int mb_order_split(const float* cost_pred, uint32_t ntiles, uint32_t 
     cudaGetLastError();
     return MB_ENOMEM;
   }
-  order_split_kernel<<<1, OS_T, 0, st>>>(cost_pred, ntiles, tile, grid, split, (uint8_t*)ws, (uint32_t*)(ws + a256(ntiles)),
+  order_split_kernel<<<1, OS_T, 0, st>>>(cost_pred, ntiles, tile, grid, split, 1u, (uint8_t*)ws,
+                                         (uint32_t*)(ws + a256(ntiles)),
                                          items, capacity, n_items, status);
   int rc = cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
   cudaFreeAsync(ws, st);
@@ -590,8 +592,9 @@ extern "C" int mb_model_load(const char* path, float* params) {
 namespace mb {
 
 int order_tiles(const uint32_t* probe, const float* feat, uint32_t nt, const float* params, uint32_t tile,
-                uint32_t grid, uint32_t split, const uint32_t* goff, const uint32_t* tx, uint32_t nviews,
-                mb_item* items, uint32_t capacity, uint32_t* n_items, uint32_t* status, cudaStream_t st) {
+                uint32_t grid, uint32_t split, uint32_t min_strips, const uint32_t* goff, const uint32_t* tx,
+                uint32_t nviews, mb_item* items, uint32_t capacity, uint32_t* n_items, uint32_t* status,
+                cudaStream_t st) {
   if (!probe || !items || !n_items || nt == 0 || grid == 0 || (params && !feat) || !goff || !tx || nviews == 0)
     return MB_EINVAL;
   if (split == 0) split = 4;
@@ -615,7 +618,8 @@ int order_tiles(const uint32_t* probe, const float* feat, uint32_t nt, const flo
   }
   if (rc == MB_OK) {
     guard_kernel<<<min((nt + 255) / 256, 4096u), 256, 0, st>>>(y, nt, goff, tx, nviews, 0u, yg);
-    order_split_kernel<<<1, OS_T, 0, st>>>(yg, nt, tile, grid, split, qbuf, order, items, capacity, n_items, status);
+    order_split_kernel<<<1, OS_T, 0, st>>>(yg, nt, tile, grid, split, min_strips, qbuf, order, items, capacity,
+                                           n_items, status);
     rc = cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
   }
   cudaFreeAsync(ws, st);
@@ -717,7 +721,7 @@ extern "C" int mb_render_learned(const mb_window* w, uint32_t m, uint32_t n, uin
   rc = check_opts(opt, &log2_tile);
   if (rc) return rc;
   const uint32_t tile = 1u << log2_tile;
-  if (tile < 16) return MB_EINVAL;
+  if (tile < 16 || !min_strips_ok(opt, tile)) return MB_EINVAL;
   const uint32_t block = opt && opt->block ? opt->block : DEFAULT_BLOCK;
   cudaStream_t st = opt ? (cudaStream_t)opt->stream : nullptr;
   const uint32_t tx = (n + tile - 1) / tile, ty = (m + tile - 1) / tile;
@@ -764,7 +768,8 @@ extern "C" int mb_render_learned(const mb_window* w, uint32_t m, uint32_t n, uin
     if (split > 4096) split = 4096;
     guard_kernel<<<min((nt + 255) / 256, 4096u), 256, 0, st>>>((const float*)(ws + lay.y), nt, nullptr, nullptr, 1u, tx,
                                                                (float*)(ws + lay.yg));
-    order_split_kernel<<<1, OS_T, 0, st>>>((const float*)(ws + lay.yg), nt, tile, grid, split, (uint8_t*)(ws + lay.qbuf),
+    order_split_kernel<<<1, OS_T, 0, st>>>((const float*)(ws + lay.yg), nt, tile, grid, split, opt_min_strips(opt, tile),
+                                           (uint8_t*)(ws + lay.qbuf),
                                            (uint32_t*)(ws + lay.order), (mb_item*)(ws + lay.items), cap,
                                            (uint32_t*)(ws + lay.nitems), P.status);
     rc = cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;

@@ -42,6 +42,8 @@ struct BatchItem {
   uint32_t tile;
   uint16_t row0, rows;
 };
+// load_item() reads both item kinds as 32-bit words, rows above row0 in the last word
+static_assert(sizeof(mb_item) == 8 && sizeof(BatchItem) == 12, "item layouts");
 
 
 // status bits
@@ -84,24 +86,47 @@ __device__ __forceinline__ void set_status(const RenderParams& P, uint32_t bits)
   if (P.status) atomicOr(P.status, bits);
 }
 
-// Pixels in item `it` (before edge clipping).
+// The words of one listed work item, read once by the claiming lane and handed
+// to the warp (KIND_LIST: mb_item; KIND_BATCH: BatchItem), so that refills do
+// not wait on a second read of the same item from global memory.
+struct ItemWords {
+  uint32_t view, tile, rr;  // rr = row0 | rows << 16
+};
+
 template <int KIND>
-__device__ __forceinline__ uint32_t item_pixels(const RenderParams& P, uint32_t it) {
+__device__ __forceinline__ ItemWords load_item(const RenderParams& P, uint32_t it) {
+  ItemWords w{0u, it, 0u};
+  if (KIND == KIND_LIST) {
+    const uint32_t* e = reinterpret_cast<const uint32_t*>(P.items + it);
+    w.tile = e[0];
+    w.rr = e[1];
+  } else if (KIND == KIND_BATCH) {
+    const uint32_t* e = reinterpret_cast<const uint32_t*>(P.bitems + it);
+    w.view = e[0];
+    w.tile = e[1];
+    w.rr = e[2];
+  }
+  return w;
+}
+
+// Pixels in item `it` (before edge clipping); `w` holds its words for listed kinds.
+template <int KIND>
+__device__ __forceinline__ uint32_t item_pixels(const RenderParams& P, const ItemWords& w) {
   if (KIND == KIND_ROWS) return P.views[0].n;
   if (KIND == KIND_RASTER) return 1u << (2 * P.log2_tile);
   if (KIND == KIND_PROBE) return PROBE_SIDE * PROBE_SIDE;
-  if (KIND == KIND_LIST) return (uint32_t)P.items[it].rows << P.log2_tile;
-  return (uint32_t)P.bitems[it].rows << P.log2_tile;
+  return (w.rr >> 16) << P.log2_tile;
 }
 
-// First item of CTA b, and the item after `it`.
+// Number of items: the host's count, or the device count a previous kernel wrote.
 __device__ __forceinline__ uint32_t item_count(const RenderParams& P) {
   return P.n_items_dev ? *(volatile const uint32_t*)P.n_items_dev : P.n_items;
 }
 
+// First item of CTA b, and the item after `it`, among N items.
 template <int SCHED>
-__device__ __forceinline__ uint32_t first_item(const RenderParams& P) {
-  uint32_t G = gridDim.x, b = blockIdx.x, N = item_count(P);
+__device__ __forceinline__ uint32_t first_item(const RenderParams& P, uint32_t N) {
+  uint32_t G = gridDim.x, b = blockIdx.x;
   if (SCHED == S_NAIVE) {  // S_b = (N/G) b; the last CTA also takes N mod G (Sec. III-A)
     uint32_t per = N / G;
     uint32_t cnt = per + (b == G - 1 ? N % G : 0);
@@ -113,8 +138,8 @@ __device__ __forceinline__ uint32_t first_item(const RenderParams& P) {
 }
 
 template <int SCHED>
-__device__ __forceinline__ uint32_t next_item(const RenderParams& P, uint32_t it) {
-  uint32_t G = gridDim.x, b = blockIdx.x, N = item_count(P);
+__device__ __forceinline__ uint32_t next_item(const RenderParams& P, uint32_t it, uint32_t N) {
+  uint32_t G = gridDim.x, b = blockIdx.x;
   if (SCHED == S_NAIVE) {
     uint32_t per = N / G;
     uint32_t last = per * (b + 1) + (b == G - 1 ? N % G : 0);
@@ -125,19 +150,21 @@ __device__ __forceinline__ uint32_t next_item(const RenderParams& P, uint32_t it
   return k < N ? k : END_ITEM;
 }
 
-// Claim up to `need` pixels for the calling warp (lane 0 only).  Returns the
-// number granted (0 = no work left) and the item / first offset.
+// Claim up to `need` pixels for the calling warp (lane 0 only) among N items.
+// Returns the number granted (0 = no work left), the item, its first offset
+// and (listed kinds) its words.
 template <int KIND, int SCHED>
-__device__ uint32_t claim(const RenderParams& P, unsigned long long* word, uint32_t* taken, uint32_t need,
-                          uint32_t& item, uint32_t& off) {
+__device__ uint32_t claim(const RenderParams& P, unsigned long long* word, uint32_t* taken, uint32_t need, uint32_t N,
+                          uint32_t& item, uint32_t& off, ItemWords& iw) {
   int spins = 0;
   for (;;) {
     unsigned long long w = atomicAdd(word, (unsigned long long)need);
     uint32_t it = (uint32_t)(w >> 32), o = (uint32_t)w;
     if (it == END_ITEM) return 0;
-    uint32_t Pn = item_pixels<KIND>(P, it);
+    ItemWords e = load_item<KIND>(P, it);
+    uint32_t Pn = item_pixels<KIND>(P, e);
     if (Pn == 0 && o == 0) {  // an empty item (rows = 0 in a list): its unique first claimer moves on
-      uint32_t nx = next_item<SCHED>(P, it);
+      uint32_t nx = next_item<SCHED>(P, it, N);
       if (nx != END_ITEM) atomicAdd(taken, 1u);
       atomicExch(word, (unsigned long long)nx << 32);
       continue;
@@ -145,8 +172,9 @@ __device__ uint32_t claim(const RenderParams& P, unsigned long long* word, uint3
     if (o < Pn) {
       item = it;
       off = o;
+      iw = e;
       if (o + need >= Pn) {  // this claim reaches the item's end: advance the CTA
-        uint32_t nx = next_item<SCHED>(P, it);
+        uint32_t nx = next_item<SCHED>(P, it, N);
         if (nx != END_ITEM) atomicAdd(taken, 1u);
         atomicExch(word, (unsigned long long)nx << 32);
         return Pn - o;
@@ -166,8 +194,8 @@ __device__ uint32_t claim(const RenderParams& P, unsigned long long* word, uint3
 
 // Map pixel `pix` of item `it` to (view, row, col); false if it lies outside the image.
 template <int KIND>
-__device__ __forceinline__ bool decode(const RenderParams& P, uint32_t it, uint32_t pix, uint32_t& v,
-                                       uint32_t& row, uint32_t& col, uint32_t& tile) {
+__device__ __forceinline__ bool decode(const RenderParams& P, uint32_t it, const ItemWords& e, uint32_t pix,
+                                       uint32_t& v, uint32_t& row, uint32_t& col, uint32_t& tile) {
   if (KIND == KIND_ROWS) {
     v = 0;
     row = it;
@@ -190,16 +218,10 @@ __device__ __forceinline__ bool decode(const RenderParams& P, uint32_t it, uint3
     v = 0;
     t = it;
     r0 = 0;
-  } else if (KIND == KIND_LIST) {
-    v = 0;
-    mb_item e = P.items[it];
+  } else {  // listed kinds: the words the claiming lane read
+    v = KIND == KIND_BATCH ? e.view : 0u;
     t = e.tile;
-    r0 = e.row0;
-  } else {
-    BatchItem e = P.bitems[it];
-    v = e.view;
-    t = e.tile;
-    r0 = e.row0;
+    r0 = e.rr & 0xFFFFu;
   }
   if ((r0 + (pix >> P.log2_tile)) >> P.log2_tile) {  // item reaches past its tile
     if (P.status) atomicOr(P.status, ST_BAD_ITEM);
@@ -225,18 +247,20 @@ __device__ __forceinline__ bool decode(const RenderParams& P, uint32_t it, uint3
 template <int KIND, int SCHED, bool FILT, int UNROLL, bool EMUL, int PREC>
 __device__ __forceinline__ void render_body(RenderParams P) {
   __shared__ unsigned long long s_word;
-  __shared__ uint32_t s_taken;
+  __shared__ uint32_t s_taken, s_items;
   __shared__ uint64_t s_t0;
   const int lane = threadIdx.x & 31;
   uint64_t t_start = 0;
   if (threadIdx.x == 0) {
     t_start = globaltimer_ns();
     s_t0 = t_start;
-    uint32_t it = first_item<SCHED>(P);
+    s_items = item_count(P);  // fixed for the launch: read once per CTA
+    uint32_t it = first_item<SCHED>(P, s_items);
     s_word = (unsigned long long)it << 32;
     s_taken = it != END_ITEM ? 1u : 0u;
   }
   __syncthreads();
+  const uint32_t n_items = s_items;
 
   typename LaneOf<PREC>::type L;
   lane_clear(L);
@@ -261,7 +285,8 @@ __device__ __forceinline__ void render_body(RenderParams P) {
     unsigned idle = __ballot_sync(FULL_MASK, !has);
     while (idle && !drained) {
       uint32_t need = __popc(idle), item = 0, off = 0, got = 0;
-      if (lane == 0) got = claim<KIND, SCHED>(P, &s_word, &s_taken, need, item, off);
+      ItemWords iw{0u, 0u, 0u};
+      if (lane == 0) got = claim<KIND, SCHED>(P, &s_word, &s_taken, need, n_items, item, off, iw);
       got = __shfl_sync(FULL_MASK, got, 0);
       if (got == 0) {
         drained = true;
@@ -269,10 +294,15 @@ __device__ __forceinline__ void render_body(RenderParams P) {
       }
       item = __shfl_sync(FULL_MASK, item, 0);
       off = __shfl_sync(FULL_MASK, off, 0);
+      if (KIND == KIND_LIST || KIND == KIND_BATCH) {
+        iw.tile = __shfl_sync(FULL_MASK, iw.tile, 0);
+        iw.rr = __shfl_sync(FULL_MASK, iw.rr, 0);
+        if (KIND == KIND_BATCH) iw.view = __shfl_sync(FULL_MASK, iw.view, 0);
+      }
       uint32_t rank = __popc(idle & ((1u << lane) - 1u));
       if (!has && rank < got) {
         uint32_t v, row, col, tile;
-        if (decode<KIND>(P, item, off + rank, v, row, col, tile)) {
+        if (decode<KIND>(P, item, iw, off + rank, v, row, col, tile)) {
           const ViewDesc& V = P.views[v];
           lane_start(L, V.cx[col], V.cy[row], V.iter_max, V.r2);
           r2 = V.r2;

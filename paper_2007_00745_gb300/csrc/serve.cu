@@ -165,7 +165,7 @@ static int learn_order_locked(mb_server* S, Req& R) {
     if (rc) return rc;
   }
   // one rank per tile: a work list without splits (one worker, split divisor 1)
-  rc = order_tiles(probe, feat, nt, S->model, S->tile, 1u, 1u, meta, meta + 2, 1u, items, nt, meta + 3, nullptr,
+  rc = order_tiles(probe, feat, nt, S->model, S->tile, 1u, 1u, 1u, meta, meta + 2, 1u, items, nt, meta + 3, nullptr,
                    S->setup);
   if (rc) return rc;
   serve_perm_kernel<<<(nt + 255) / 256 < 1024 ? (nt + 255) / 256 : 1024, 256, 0, S->setup>>>(

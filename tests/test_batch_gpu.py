@@ -120,6 +120,12 @@ def test_batch_learned_order(orc, model, tile):
     plan.launch()
     _check(orc, vs, outs)
     plan.destroy()
+    outs = _outs(vs)
+    plan = mb.BatchPlan(vs, outs, tile=tile, block=512, learned_order=1, model=params, min_strips=4)
+    assert plan.info()["items"] >= 4 * n_tiles        # every tile in at least 4 strips
+    plan.launch()
+    _check(orc, vs, outs)
+    plan.destroy()
 
 
 def test_batch_learned_order_needs_tile_16():

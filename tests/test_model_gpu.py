@@ -198,6 +198,24 @@ def test_learned_render_is_bit_exact(orc, small_model, tile):
     assert np.array_equal(_u32(out).reshape(v.m, v.n), orc.render(v.window, v.m, v.n, v.iter_max, v.r2))
 
 
+@pytest.mark.parametrize("tile,min_strips", [(32, 4), (64, 16), (16, 2)])
+def test_learned_render_min_strips_is_bit_exact(orc, small_model, tile, min_strips):
+    """Every tile cut into at least min_strips strips: still the oracle's image."""
+    params = small_model[0]
+    v = wl.View(wl.zoom_window(-0.74364, 0.13182, 3e-5, 301, 389), 301, 389, 5000)
+    out = torch.full((v.m * v.n,), -1, dtype=torch.int32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    mb.mb_render_learned(v.window, v.m, v.n, v.iter_max, v.r2, out, params, tile=tile, min_strips=min_strips,
+                         status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert np.array_equal(_u32(out).reshape(v.m, v.n), orc.render(v.window, v.m, v.n, v.iter_max, v.r2))
+    for bad in (3, 32, tile * 2 if tile < 16 else 0):
+        if bad:
+            with pytest.raises(mb.MBError):
+                mb.mb_render_learned(v.window, v.m, v.n, v.iter_max, v.r2, out, params, tile=tile, min_strips=bad)
+
+
 def _time_ms(fn, reps=3):
     best = 1e30
     for _ in range(reps):

@@ -166,3 +166,15 @@ def test_guard_properties():
     assert (g[max(i - 1, 0):i + 2, max(j - 1, 0):j + 2] == y.max()).all()   # the peak spreads one tile
     one = M.guard_costs(np.array([0.3], np.float32), 1, 1)
     assert one.tolist() == pytest.approx([0.3])
+
+
+def test_min_strips_hand_example():
+    # same three tiles, min_strips 4: tiles 0 and 2 become 4 strips of 16 rows; tile 1 still
+    # needs 8 (target 8256 as above) and gets 8 strips of 8 rows
+    items = M.order_and_split([0.25, 0.5, 0.25], 64, 2, min_strips=4)
+    assert items[:8] == [(1, 8 * k, 8) for k in range(8)]
+    assert items[8:] == [(0, 16 * k, 16) for k in range(4)] + [(2, 16 * k, 16) for k in range(4)]
+    # min_strips above the usual cap wins: 16 strips of 2 rows for a 32-row tile whose cap is 8
+    assert M.order_and_split([0.25], 32, 1, min_strips=16) == [(0, 2 * k, 2) for k in range(16)]
+    # min_strips 1 is the plain rule
+    assert M.order_and_split([0.25, 0.5, 0.25], 64, 2, min_strips=1) == M.order_and_split([0.25, 0.5, 0.25], 64, 2)
