@@ -54,13 +54,15 @@ def train(X, y, epochs=40, batch=256, lr=2e-3, seed=wl.SEED + 6, stream=None):
     return params, loss
 
 
-def default_model(train_views=64, side=1024, tile=32, epochs=200, lr=1e-3, stream=None, cache=True):
+def default_model(train_views=64, side=1024, tile=32, epochs=200, lr=1e-3, stream=None, cache=True, wide_views=16):
     """The trained model used by the benchmark: trained on seeded zoom views
-    (training_zoom_views) at the tile size it will order (its probe-sum feature
-    scales with the tile area), cached under _build/ keyed by its recipe."""
+    (training_zoom_views) and seeded whole-set views (training_wide_views) at the
+    tile size it will order (its probe-sum feature scales with the tile area),
+    cached under _build/ keyed by its recipe.  No training view is one of the
+    benchmark's windows."""
     import torch
-    recipe = {"views": train_views, "side": side, "tile": tile, "epochs": epochs, "lr": lr, "seed": wl.SEED,
-              "lib": mb.mb_version(), "features": "probe-sum-residual-v3"}
+    recipe = {"views": train_views, "wide": wide_views, "side": side, "tile": tile, "epochs": epochs, "lr": lr,
+              "seed": wl.SEED, "lib": mb.mb_version(), "features": "probe-sum-residual-v4"}
     key = hashlib.sha1(json.dumps(recipe, sort_keys=True).encode()).hexdigest()[:12]
     path = os.path.join(CACHE_DIR, "tile_model_%s.bin" % key)
     params = torch.empty(mb.MB_MLP_PARAMS, dtype=torch.float32, device="cuda")
@@ -70,7 +72,8 @@ def default_model(train_views=64, side=1024, tile=32, epochs=200, lr=1e-3, strea
             return params, None
         except mb.MBError:
             pass   # unreadable or foreign file: train afresh
-    X, y = build_training_set(wl.training_zoom_views(train_views, side), tile, stream=stream)
+    views = wl.training_zoom_views(train_views, side) + wl.training_wide_views(wide_views, side)
+    X, y = build_training_set(views, tile, stream=stream)
     params, loss = train(X, y, epochs=epochs, lr=lr, stream=stream)
     if cache:
         os.makedirs(CACHE_DIR, exist_ok=True)

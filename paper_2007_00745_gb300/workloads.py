@@ -92,6 +92,23 @@ def training_zoom_views(count, side, seed=SEED + 3, iter_max_range=(2048, 32768)
     return out
 
 
+def training_wide_views(count, side, seed=SEED + 10, iter_max_range=(2048, 32768)):
+    """Seeded windows showing the whole set (centre near -0.75 + 0i, width 2.5 .. 3.5,
+    square), for training the tile-cost model on the kind of view the full-set
+    benchmark renders: random centres, widths and budgets, so that none is the
+    benchmark's own window or grid."""
+    rng = SplitMix64(seed)
+    out = []
+    for _ in range(count):
+        cx = -0.75 + 0.5 * (rng.uniform() - 0.5)
+        cy = 0.5 * (rng.uniform() - 0.5)
+        width = 2.5 + rng.uniform()
+        it = int(round(2.0 ** (math.log2(iter_max_range[0]) + rng.uniform()
+                               * (math.log2(iter_max_range[1]) - math.log2(iter_max_range[0])))))
+        out.append(View(zoom_window(cx, cy, width, side, side), side, side, it))
+    return out
+
+
 def boundary_points():
     """Centres near the set's boundary: pixels of a 1024^2 full-view render
     (re[-2,1] im[-1.5,1.5], iterMax 65536) with count in [50, 65536), as

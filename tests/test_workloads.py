@@ -152,3 +152,14 @@ def test_random_feature_and_cost_ranges():
     assert f.shape == (300, 70) and f.dtype == np.float32 and f.min() >= 0.0 and f.max() < 1.0
     c = wl.random_costs(1000)
     assert c.dtype == np.float32 and c.min() >= -0.05 and c.max() <= 0.95
+
+
+def test_training_wide_views_recipe():
+    vs = wl.training_wide_views(16, 1024)
+    assert vs == wl.training_wide_views(16, 1024) and len(vs) == 16
+    for v in vs:
+        x0, x1, y0, y1 = v.window
+        assert 2.5 <= x1 - x0 <= 3.5 and abs((y1 - y0) - (x1 - x0)) < 1e-12
+        assert -1.0 <= (x0 + x1) / 2 <= -0.5 and abs((y0 + y1) / 2) <= 0.25
+        assert 2048 <= v.iter_max <= 32768 and v.m == v.n == 1024
+        assert v.window != wl.FULL_VIEW_2.window
