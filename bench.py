@@ -51,8 +51,8 @@ FP64_PIPE_OPS_PER_ITER = 2.5
 # scales by pixel count) and the busy fraction of each pipe the step is split
 # across, so that the binding pipes are visible beside the FP64 roofline; used
 # only while the kernel sources still hash to src_sha1, else null.
-NCU_RENDER = {"src_sha1": "33d84c29cdf0a2d3dd5ce118fefe6dd268caffcf", "dram_bytes_per_pixel": 3.868,
-              "pipes": {"fp64": 0.784, "alu": 0.805, "fma": 0.267, "issue": 0.712}}
+NCU_RENDER = {"src_sha1": "bc9673f8bce11ced2c8ad63c4f07ac1a3053585d", "dram_bytes_per_pixel": 3.866,
+              "pipes": {"fp64": 0.800, "alu": 0.804, "fma": 0.273, "issue": 0.717}}
 KERNEL_SOURCES = ("escape_core.cuh", "escape_lowp.cuh", "render_kernels.cuh")
 
 

@@ -296,6 +296,24 @@ def test_trained_network_beats_the_probe_sum_on_held_out_views():
     assert rho_net > rho_ps - 1e-3
 
 
+def test_trained_network_on_held_out_whole_set_views():
+    """The same comparison on 8 held-out whole-set views (a seed never trained
+    on), the kind of view the headline benchmark renders."""
+    params, _ = tilemodel.default_model()
+    held = wl.training_wide_views(8, 1024, seed=wl.SEED + 998)
+    X, y = tilemodel.build_training_set(held, 32)
+    n = X.shape[0]
+    pred = torch.empty(n, dtype=torch.float32, device="cuda")
+    mb.mb_mlp_forward(params, X, n, pred)
+    torch.cuda.synchronize()
+    t = y.cpu().numpy().astype(np.float64)
+    net = pred.cpu().numpy().astype(np.float64)
+    ps = X[:, 68].cpu().numpy().astype(np.float64)
+    mse_net, mse_ps = float(np.mean((net - t) ** 2)), float(np.mean((ps - t) ** 2))
+    print("held-out whole-set MSE network %.3g, probe-sum %.3g" % (mse_net, mse_ps))
+    assert mse_net < mse_ps
+
+
 @pytest.mark.parametrize("tx,ty", [(1, 1), (1, 7), (9, 1), (37, 23), (256, 256)])
 def test_guard_parity(tx, ty):
     """mb_guard_costs equals the oracle's neighbourhood guard exactly (a max of
