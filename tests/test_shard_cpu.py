@@ -182,3 +182,47 @@ def test_dispatcher_hands_out_each_chunk_once():
 def test_tile_items_cover_whole_tiles():
     items = shard.tile_items([3, 0, 7], 32)
     assert items.tolist() == [[3, 32 << 16], [0, 32 << 16], [7, 32 << 16]]
+
+
+_TORCHRUN_SCRIPT = r'''
+import os, sys, json
+sys.path.insert(0, os.environ["MB_ROOT"])
+import torch, torch.distributed as dist
+from paper_2007_00745_gb300 import shard
+rank, world = int(os.environ["RANK"]), int(os.environ["WORLD_SIZE"])
+store = shard.make_store(rank, world)
+dist.init_process_group("gloo", store=store, rank=rank, world_size=world)
+disp = shard.ChunkDispatcher(store, "t", 40, 4)
+mine = []
+while True:
+    g = disp.next()
+    if g is None:
+        break
+    mine.append(g[0])
+got = [None] * world
+dist.all_gather_object(got, mine)
+if rank == 0:
+    print(json.dumps(got))
+dist.barrier()
+dist.destroy_process_group()
+'''
+
+
+def test_dispatcher_under_torchrun(tmp_path):
+    """Under torchrun the launcher's agent hosts the store (every rank connects
+    as a client): the dispatcher hands each of the 10 chunks to exactly one of
+    the 2 ranks, and the process group shares that store."""
+    import json
+    import subprocess
+    import sys
+    script = tmp_path / "disp.py"
+    script.write_text(_TORCHRUN_SCRIPT)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, MB_ROOT=root)
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), str(script)]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=300, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = [ln for ln in r.stdout.splitlines() if ln.startswith("[")][0]
+    got = json.loads(line)
+    assert sorted(c for part in got for c in part) == list(range(10))
