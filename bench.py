@@ -66,7 +66,7 @@ def parse():
                    help="learned (default) or a plain scheduler: naive, alternating, fcfs_rows, fcfs_tiles")
     p.add_argument("--tile", type=int, default=32)
     p.add_argument("--block", type=int, default=512)
-    p.add_argument("--unroll", type=int, default=8)
+    p.add_argument("--unroll", type=int, default=4)
     p.add_argument("--min-strips", type=int, default=1,
                    help="learned order: cut every tile into at least this many row strips (power of two)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -746,7 +746,8 @@ def run_ours(args):
         cmp = {}
         variants = [("naive", dict(sched="naive", tile=64)), ("alternating", dict(sched="alternating", tile=64)),
                     ("fcfs_rows", dict(sched="fcfs_rows", tile=64)), ("fcfs_tiles64", dict(sched="fcfs_tiles", tile=64)),
-                    ("fcfs_tiles16", dict(sched="fcfs_tiles", tile=16)), ("learned", None), ("probe_sum", "probe"),
+                    ("fcfs_tiles32", dict(sched="fcfs_tiles", tile=32)), ("fcfs_tiles16", dict(sched="fcfs_tiles", tile=16)),
+                    ("learned", None), ("probe_sum", "probe"),
                     ("learned64", "learned64")]
         params64 = tilemodel.default_model(tile=64, stream=stream)[0] if params is not None else None
         for name, kw in variants:

@@ -107,7 +107,7 @@ typedef struct {
   uint32_t tile;             /* tile side, a power of two in [8, 256]; 0 = 64 */
   uint32_t grid;             /* CTAs; 0 = SM count x resident CTAs per SM */
   uint32_t block;            /* threads per CTA, multiple of 32 in [32, 512]; 0 = 256 */
-  uint32_t unroll;           /* escape steps between lane refills: 4, 8 or 16; 0 = 8.  The cycle-detection and
+  uint32_t unroll;           /* escape steps between lane refills: 4, 8 or 16; 0 = 4.  The cycle-detection and
                                 reduced-precision kernels use 16 when 16 is asked, else 8; a binary32 step is
                                 four iterations */
   void* stream;              /* cudaStream_t; NULL = legacy default stream */
@@ -307,7 +307,7 @@ typedef struct {
 
 typedef struct mb_server mb_server;
 
-/* opts: tile (default 32), block (512), unroll (8), grid, round_tiles, precision and
+/* opts: tile (default 32), block (512), unroll (4), grid, round_tiles, precision and
  * cycle_check (as for mb_render, applied to every request), learned_order and
  * model (not in the paper: each admitted request is probed once, 8 x 8 samples
  * per tile written into its counts, its tiles' costs predicted by `model` or the

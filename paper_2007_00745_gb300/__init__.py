@@ -384,7 +384,7 @@ class Server:
     """mb_serve_*: continuous-batching render server under a device-memory budget.
 
     Options (keyword arguments, as for mb_render): tile (32), block (512),
-    unroll (8), grid, round_tiles (tiles per round; 0 = 16 x grid), precision
+    unroll (4), grid, round_tiles (tiles per round; 0 = 16 x grid), precision
     ("fp64", "fp32", "dfloat") and cycle_check, applied to every request.
     queue_limit 0 = 1024 waiting requests."""
 

@@ -432,7 +432,7 @@ extern "C" int mb_batch_autotune(const mb_view* views, uint32_t count, const mb_
   for (uint32_t i = 0; i < count; i += sample_stride) sample.push_back(views[i]);
   const uint32_t tiles[] = {16, 32, 64};
   const uint32_t blocks[] = {256, 512};
-  const uint32_t unrolls[] = {8, 16};
+  const uint32_t unrolls[] = {4, 8, 16};
   float best_t = 1e30f;
   mb_opts winner = b;
   cudaEvent_t e0, e1;

@@ -91,6 +91,8 @@ struct mb_server {
   mb::ViewDesc* h_view_stage = nullptr;  // pinned
   cudaStream_t setup = nullptr, streams[mb::SERVE_STREAMS] = {};
   cudaEvent_t setup_ev = nullptr;
+  std::vector<cudaEvent_t> slot_ev;  // per view slot: the admitted request's set-up work is done
+  bool setup_pending = false;        // a live request's set-up was still running at the last round
   cudaMemPool_t pool = nullptr;  // the server's own pool: freed request memory stays reserved for the next ones
   mb::Round rounds[mb::SERVE_STREAMS];
   mb::RenderFn fn_filt = nullptr, fn_exact = nullptr, fn_probe_filt = nullptr, fn_probe_exact = nullptr;
@@ -178,7 +180,9 @@ static size_t req_bytes(const mb_server* S, const mb_request& r) {
 }
 
 // Admit queued requests that fit (caller holds the lock).  Device work is
-// enqueued on the setup stream; the next rounds wait for its event.
+// enqueued on the setup stream and followed by the request's slot event; a
+// round takes a request's tiles only once that event has completed, so no
+// round waits for another request's set-up (its probe, with the learned order).
 static int admit_locked(mb_server* S) {
   bool any = false;
   while (!S->queue.empty() && !S->free_slots.empty()) {
@@ -218,6 +222,9 @@ static int admit_locked(mb_server* S) {
       int rc = learn_order_locked(S, R);
       if (rc) return rc;
     }
+    if (!S->slot_ev[R.slot] && cudaEventCreateWithFlags(&S->slot_ev[R.slot], cudaEventDisableTiming) != cudaSuccess)
+      return MB_ECUDA;
+    if (cudaEventRecord(S->slot_ev[R.slot], S->setup) != cudaSuccess) return MB_ECUDA;
     R.state = RQ_LIVE;
     R.admit_ns = now_ns();
     S->live.push_back(R.id);
@@ -235,8 +242,19 @@ static int launch_round_locked(mb_server* S, int k, bool* launched) {
   uint32_t nit = 0;
   Rd.parts.clear();
   uint64_t t = now_ns();
+  S->setup_pending = false;
   for (auto it = S->live.begin(); it != S->live.end() && nit < S->round_tiles;) {
     Req& R = S->reqs[*it];
+    cudaError_t q = cudaEventQuery(S->slot_ev[R.slot]);
+    if (q == cudaErrorNotReady) {  // its set-up is still running: it joins a later round
+      S->setup_pending = true;
+      ++it;
+      continue;
+    }
+    if (q != cudaSuccess) {
+      cudaGetLastError();
+      return MB_ECUDA;
+    }
     uint32_t take = std::min(R.tiles - R.next_tile, S->round_tiles - nit);
     for (uint32_t j = 0; j < take; ++j) {
       BatchItem b;
@@ -257,8 +275,7 @@ static int launch_round_locked(mb_server* S, int k, bool* launched) {
   }
   if (nit == 0) return MB_OK;
   cudaStream_t st = S->streams[k];
-  if (cudaStreamWaitEvent(st, S->setup_ev, 0) != cudaSuccess ||
-      cudaMemcpyAsync(Rd.d_items, Rd.h_items, (size_t)nit * sizeof(BatchItem), cudaMemcpyHostToDevice, st) !=
+  if (cudaMemcpyAsync(Rd.d_items, Rd.h_items, (size_t)nit * sizeof(BatchItem), cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
       cudaMemsetAsync(Rd.d_counter, 0, 4, st) != cudaSuccess)
     return MB_ECUDA;
@@ -291,6 +308,7 @@ static void fail_all_locked(mb_server* S, int code) {
   }
   S->queue.clear();
   S->live.clear();
+  S->setup_pending = false;
   S->cv_done.notify_all();
 }
 
@@ -349,8 +367,8 @@ static void worker_main(mb_server* S) {
       }
       S->cv_done.notify_all();
     }
-    if (S->stop && !busy && !launched_any) break;
-    if (busy || launched_any) {
+    if (S->stop && !busy && !launched_any && !S->setup_pending) break;
+    if (busy || launched_any || S->setup_pending) {
       // poll the in-flight rounds without holding the lock for long
       lk.unlock();
       std::this_thread::sleep_for(std::chrono::microseconds(100));
@@ -374,7 +392,7 @@ extern "C" int mb_serve_create(size_t mem_budget_bytes, uint32_t queue_limit, co
   if (opt) o = *opt;
   if (!o.tile) o.tile = 32;
   if (!o.block) o.block = 512;
-  if (!o.unroll) o.unroll = 8;
+  if (!o.unroll) o.unroll = 4;
   int rc = check_opts(&o, &log2_tile, ALLOW_CYCLE | ALLOW_PRECISION);
   if (rc) return rc;
   if (o.learned_order && o.tile < 16) return MB_EINVAL;  // the probe takes 8 x 8 samples per tile
@@ -430,6 +448,7 @@ extern "C" int mb_serve_create(size_t mem_budget_bytes, uint32_t queue_limit, co
     return MB_ENOMEM;
   }
   for (uint32_t k = 0; k < SERVE_SLOTS; ++k) S->free_slots.push_back(SERVE_SLOTS - 1 - k);
+  S->slot_ev.assign(SERVE_SLOTS, nullptr);
   S->worker = std::thread(worker_main, S);
   *out = S;
   return MB_OK;
@@ -598,6 +617,8 @@ extern "C" int mb_serve_destroy(mb_server* S) {
     if (S->streams[k]) cudaStreamDestroy(S->streams[k]);
   }
   if (S->setup_ev) cudaEventDestroy(S->setup_ev);
+  for (cudaEvent_t e : S->slot_ev)
+    if (e) cudaEventDestroy(e);
   if (S->setup) cudaStreamDestroy(S->setup);
   if (S->d_views) cudaFree(S->d_views);
   if (S->d_probe_counter) cudaFree(S->d_probe_counter);

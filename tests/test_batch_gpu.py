@@ -78,7 +78,7 @@ def test_autotune_and_cache(orc):
     with tempfile.TemporaryDirectory() as d:
         path = os.path.join(d, "tune.txt")
         best, ms = mb.mb_batch_autotune(vs, outs, sample_stride=1, cache_path=path)
-        assert best["tile"] in (16, 32, 64) and best["block"] in (256, 512) and best["unroll"] in (8, 16)
+        assert best["tile"] in (16, 32, 64) and best["block"] in (256, 512) and best["unroll"] in (4, 8, 16)
         assert ms > 0 and os.path.exists(path)
         best2, ms2 = mb.mb_batch_autotune(vs, outs, sample_stride=1, cache_path=path)
         assert best2 == best and abs(ms2 - ms) < 1e-3
