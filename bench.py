@@ -13,7 +13,8 @@ are formed exactly on the integer pipes), so the attainable rate is the
 measured issue rate x 8/2.5.
 
 Beside the headline (outside the timed region, rank 0 only): the paper's three
-row schedulers and plain tile FCFS on the same view (makespan, idle tail), the
+row schedulers and plain tile FCFS on the same view (makespan, idle tail) beside
+the learned order and the exact longest-first order of the same tiles, the
 end-to-end figure through host buffers, the paper's computation / total timing
 with the PPM file, the 640 x 480 naive view, the binary32 and double-float
 variants (their own rates and how many pixels differ from binary64), exact
@@ -50,9 +51,10 @@ FP64_PIPE_OPS_PER_ITER = 2.5
 # read + write per launch / pixels; traffic does not depend on iterMax, so it
 # scales by pixel count) and the busy fraction of each pipe the step is split
 # across, so that the binding pipes are visible beside the FP64 roofline; used
-# only while the kernel sources still hash to src_sha1, else null.
-NCU_RENDER = {"src_sha1": "bc9673f8bce11ced2c8ad63c4f07ac1a3053585d", "dram_bytes_per_pixel": 3.866,
-              "pipes": {"fp64": 0.800, "alu": 0.804, "fma": 0.273, "issue": 0.717}}
+# only while the kernel sources still hash to src_sha1 and the run uses the
+# captured unroll, else null.
+NCU_RENDER = {"src_sha1": "bc9673f8bce11ced2c8ad63c4f07ac1a3053585d", "unroll": 4, "dram_bytes_per_pixel": 3.876,
+              "pipes": {"fp64": 0.802, "alu": 0.795, "fma": 0.280, "issue": 0.732}}
 KERNEL_SOURCES = ("escape_core.cuh", "escape_lowp.cuh", "render_kernels.cuh")
 
 
@@ -656,7 +658,7 @@ def run_ours(args):
     render_iters = iters - probe_iters
     traffic = None
     pipes = None
-    if NCU_RENDER["src_sha1"] and NCU_RENDER["src_sha1"] == kernel_sha1():
+    if NCU_RENDER["src_sha1"] == kernel_sha1() and NCU_RENDER["unroll"] == args.unroll:
         traffic = NCU_RENDER["dram_bytes_per_pixel"] * v.m * v.n
         pipes = NCU_RENDER["pipes"]
     line = {
@@ -748,8 +750,21 @@ def run_ours(args):
                     ("fcfs_rows", dict(sched="fcfs_rows", tile=64)), ("fcfs_tiles64", dict(sched="fcfs_tiles", tile=64)),
                     ("fcfs_tiles32", dict(sched="fcfs_tiles", tile=32)), ("fcfs_tiles16", dict(sched="fcfs_tiles", tile=16)),
                     ("learned", None), ("probe_sum", "probe"),
-                    ("learned64", "learned64")]
+                    ("learned64", "learned64"), ("lpt_exact16", ("lpt", 16)), ("lpt_exact32", ("lpt", 32))]
         params64 = tilemodel.default_model(tile=64, stream=stream)[0] if params is not None else None
+        # the bound on any ordering: tiles longest-first by their true cost (per-tile totals of an
+        # untimed render), which no prediction can beat
+        lpt_items = {}
+        for T in (16, 32):
+            tt = torch.zeros((-(-v.m // T)) * (-(-v.n // T)), dtype=torch.int64, device=dev)
+            mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, out, sched="fcfs_tiles", tile=T, tile_totals=tt,
+                         block=args.block, unroll=args.unroll, stream=stream)
+            torch.cuda.synchronize()
+            order = torch.argsort(tt, descending=True, stable=True)
+            it = torch.empty((order.numel(), 2), dtype=torch.int32, device=dev)
+            it[:, 0] = order.to(torch.int32)
+            it[:, 1] = T << 16
+            lpt_items[T] = it
         for name, kw in variants:
             if kw in (None, "learned64") and params is None:
                 continue
@@ -764,6 +779,11 @@ def run_ours(args):
                 mb.mb_render_learned(v.window, v.m, v.n, v.iter_max, v.r2, out, params64, tile=64,
                                      block=args.block, unroll=args.unroll, grid=g, trace=tr, min_strips=16,
                                      stream=stream)
+            elif isinstance(kw, tuple):        # exact longest-first order (the bound), no probe
+                T = kw[1]
+                mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, out, sched="fcfs_items", items=lpt_items[T],
+                             n_items=int(lpt_items[T].shape[0]), tile=T, block=args.block, unroll=args.unroll,
+                             grid=g, trace=tr, stream=stream)
             else:
                 mb.mb_render(v.window, v.m, v.n, v.iter_max, v.r2, out, block=args.block, unroll=args.unroll,
                              grid=g, trace=tr, stream=stream, **kw)
@@ -774,6 +794,10 @@ def run_ours(args):
             st["giter_s"] = iters / (st["ms"] * 1e-3) / 1e9
             cmp[name] = st
         line["schedulers"] = cmp
+        line["schedulers_note"] = ("makespan = first CTA start to last CTA end of the render kernel; ms = the whole call "
+                                   "(learned, probe_sum and learned64 include the probe and the ordering); "
+                                   "lpt_exact16/32 = the same tiles queued longest-first by their true cost (from an "
+                                   "untimed render's per-tile totals): the bound on any ordering of those tiles")
         # the small plain-method view (640 x 480, iterMax 1000, naive rows).  With the default grid
         # (G CTAs) the paper's remainder rule (Sec. III-A) gives floor(480 / G) rows to each CTA and the
         # m mod G remaining rows to the last one, so the launch is that CTA's serial tail; the paper's
