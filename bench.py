@@ -93,6 +93,7 @@ def parse():
     p.add_argument("--ppm", default="", help="also write the headline image there (default: a temporary file)")
     p.add_argument("--size", type=int, default=0, help="override m = n (profiling runs)")
     p.add_argument("--iter-max", type=int, default=0, help="override iterMax (profiling runs)")
+    p.add_argument("--window", default="", help="override the window: xmin,xmax,ymin,ymax (profiling runs)")
     p.add_argument("--cpu-rows-stride", type=int, default=4,
                    help="the CPU oracle legs (cpu_baseline and --impl reference) time every k-th row of the view")
     p.add_argument("--cpu-reps", type=int, default=3, help="repetitions of the cpu_baseline row sample")
@@ -109,13 +110,19 @@ def bench_view(args):
     v = wl.FULL_VIEW_2
     if args.size or args.iter_max:
         v = wl.scaled(v, args.size or v.m, args.size or v.n, args.iter_max or v.iter_max)
+    if args.window:
+        w = tuple(float(x) for x in args.window.split(","))
+        if len(w) != 4 or not (w[0] < w[1] and w[2] < w[3]):
+            raise SystemExit("--window wants xmin,xmax,ymin,ymax with xmin < xmax and ymin < ymax")
+        v = wl.View(w, v.m, v.n, v.iter_max, v.r2)
     return v
 
 
 def bench_config(args, v, ws):
     """The workload of both arms (ours and --impl reference): the same dict in both JSON lines."""
-    return {"workload": "%dx%d re[-2,1] im[-1.5,1.5] iterMax %d R2 4, %s (tile %d%s, block %d, unroll %d)"
-                        % (v.m, v.n, v.iter_max, "learned FCFS" if args.sched == "learned" else args.sched,
+    return {"workload": "%dx%d re[%g,%g] im[%g,%g] iterMax %d R2 %g, %s (tile %d%s, block %d, unroll %d)"
+                        % (v.m, v.n, v.window[0], v.window[1], v.window[2], v.window[3], v.iter_max, v.r2,
+                           "learned FCFS" if args.sched == "learned" else args.sched,
                            args.tile, ", %d strips per tile at least" % args.min_strips
                            if args.sched == "learned" else "", args.block, args.unroll),
             "l2": "counts %.0f MB per step %s 129 MB L2 (compute-bound)"
