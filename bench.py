@@ -805,6 +805,29 @@ def run_ours(args):
                                    "(learned, probe_sum and learned64 include the probe and the ordering); "
                                    "lpt_exact16/32 = the same tiles queued longest-first by their true cost (from an "
                                    "untimed render's per-tile totals): the bound on any ordering of those tiles")
+        if params64 is not None:
+            # where the order matters: the same size and budget with the set's interior in the last
+            # rows of the raster order; raster FCFS over 64-pixel tiles against the learned order of
+            # the same tiles (probe included), and raster FCFS over 16-pixel tiles
+            hv = wl.View(wl.HEAVY_LAST.window, v.m, v.n, v.iter_max, v.r2)
+            hres = {}
+            for name, kw in (("fcfs_tiles64", dict(sched="fcfs_tiles", tile=64)),
+                             ("learned64", None), ("fcfs_tiles16", dict(sched="fcfs_tiles", tile=16))):
+                a, b = E(), E()
+                a.record(stream)
+                if kw is None:
+                    mb.mb_render_learned(hv.window, hv.m, hv.n, hv.iter_max, hv.r2, out, params64, tile=64,
+                                         block=args.block, unroll=args.unroll, grid=g, min_strips=16, stream=stream)
+                else:
+                    mb.mb_render(hv.window, hv.m, hv.n, hv.iter_max, hv.r2, out, block=args.block,
+                                 unroll=args.unroll, grid=g, stream=stream, **kw)
+                b.record(stream)
+                torch.cuda.synchronize()
+                hres[name] = {"ms": a.elapsed_time(b)}
+            line["order_heavy_last"] = dict(
+                hres, window=list(hv.window),
+                note="the set's interior in the last rows of the raster order: raster FCFS over 64-pixel tiles "
+                     "ends on its heaviest tiles; the learned order (probe included) takes them first")
         # the small plain-method view (640 x 480, iterMax 1000, naive rows).  With the default grid
         # (G CTAs) the paper's remainder rule (Sec. III-A) gives floor(480 / G) rows to each CTA and the
         # m mod G remaining rows to the last one, so the launch is that CTA's serial tail; the paper's

@@ -42,6 +42,10 @@ FULL_VIEW_2 = View((-2.0, 1.0, -1.5, 1.5), 8192, 8192, 10000)
 # 16384^2 zoom at (-0.743643887037151, 0.131825904205330), width 1e-5, iterMax 50000.
 ZOOM_CENTRE = (-0.743643887037151, 0.131825904205330)
 ZOOM_3 = View(zoom_window(ZOOM_CENTRE[0], ZOOM_CENTRE[1], 1e-5, 16384, 16384), 16384, 16384, 50000)
+# Config 2's size and budget with the window shifted up so that the set's interior fills the
+# last rows of the raster order (re[-2, 1] im[-0.6, 2.4]): raster FCFS over coarse tiles ends on
+# its heaviest tiles, which a longest-first order takes first.
+HEAVY_LAST = View((-2.0, 1.0, -0.6, 2.4), 8192, 8192, 10000)
 # The paper's own test shape (Sec. IV): 8000 x 8000, 2000 iterations, escape radius 400
 # (read as R^2 = 400^2); its window is not stated, config 2's is used.
 PAPER_SHAPE = View((-2.0, 1.0, -1.5, 1.5), 8000, 8000, 2000, 400.0 ** 2)
