@@ -85,7 +85,7 @@ def parse():
     p.add_argument("--table2", action="store_true",
                    help="add the GPU analogue of the paper's Table II: speed-up over one worker (CTA) of the "
                         "naive, alternating and FCFS row schemes on the paper's test shape (2000^2 sample)")
-    p.add_argument("--serve-sweep", default="10,20,40,80,200,1000",
+    p.add_argument("--serve-sweep", default="10,20,40,50,80,100,200,500,1000,2000",
                    help="comma-separated request rates (1/s) of the serving sweep ('' = none); one fixed draw of "
                         "--serve-sweep-count requests is replayed at every rate")
     p.add_argument("--serve-sweep-count", type=int, default=200)
