@@ -64,11 +64,13 @@ void stats_cancel();
 // probe counts (tiles x 64) -- after the neighbourhood guard (mb_guard_costs) within each
 // view: view v owns tiles goff[v] .. goff[v+1]-1, tx[v] per row (device arrays; goff NULL:
 // one view, tx[0] on the host side is not read -- pass goff and tx for several views).
-// Temporaries are stream-ordered allocations on `st`.
+// Temporaries live in `ws` when given (order_tiles_ws_bytes(nt) bytes, 256-byte aligned,
+// not in use by other work on other streams), else in stream-ordered allocations on `st`.
 int order_tiles(const uint32_t* probe, const float* feat, uint32_t nt, const float* params, uint32_t tile,
                 uint32_t grid, uint32_t split, uint32_t min_strips, const uint32_t* goff, const uint32_t* tx,
                 uint32_t nviews, mb_item* items, uint32_t capacity, uint32_t* n_items, uint32_t* status,
-                cudaStream_t st);
+                cudaStream_t st, void* ws = nullptr);
+size_t order_tiles_ws_bytes(uint32_t nt);
 
 // Smallest number of strips a tile is cut into by the learned order (mb_opts.min_strips):
 // 0 -> 1; callers validate it with min_strips_ok().

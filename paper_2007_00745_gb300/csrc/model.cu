@@ -591,17 +591,18 @@ extern "C" int mb_model_load(const char* path, float* params) {
 
 namespace mb {
 
+size_t order_tiles_ws_bytes(uint32_t nt) { return 2 * a256((size_t)nt * 4) + a256(nt) + a256((size_t)nt * 4); }
+
 int order_tiles(const uint32_t* probe, const float* feat, uint32_t nt, const float* params, uint32_t tile,
                 uint32_t grid, uint32_t split, uint32_t min_strips, const uint32_t* goff, const uint32_t* tx,
                 uint32_t nviews, mb_item* items, uint32_t capacity, uint32_t* n_items, uint32_t* status,
-                cudaStream_t st) {
+                cudaStream_t st, void* ws_given) {
   if (!probe || !items || !n_items || nt == 0 || grid == 0 || (params && !feat) || !goff || !tx || nviews == 0)
     return MB_EINVAL;
   if (split == 0) split = 4;
   if (split > 4096) split = 4096;
-  size_t bytes = 2 * a256((size_t)nt * 4) + a256(nt) + a256((size_t)nt * 4);
-  char* ws = nullptr;
-  if (cudaMallocAsync((void**)&ws, bytes, st) != cudaSuccess) {
+  char* ws = (char*)ws_given;
+  if (!ws && cudaMallocAsync((void**)&ws, order_tiles_ws_bytes(nt), st) != cudaSuccess) {
     cudaGetLastError();
     return MB_ENOMEM;
   }
@@ -622,7 +623,7 @@ int order_tiles(const uint32_t* probe, const float* feat, uint32_t nt, const flo
                                            n_items, status);
     rc = cudaGetLastError() == cudaSuccess ? MB_OK : MB_ECUDA;
   }
-  cudaFreeAsync(ws, st);
+  if (!ws_given) cudaFreeAsync(ws, st);
   return rc;
 }
 
