@@ -167,3 +167,4 @@ def test_learned_order_serves_the_same_counts(orc, model):
     srv.destroy()
     with pytest.raises(mb.MBError):
         mb.Server(budget_bytes=1 << 20, tile=8, learned_order=1)     # the probe needs tiles of 16 or more
+
