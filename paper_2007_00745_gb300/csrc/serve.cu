@@ -93,7 +93,6 @@ struct mb_server {
   mb::ViewDesc* d_views = nullptr;
   mb::ViewDesc* h_view_stage = nullptr;  // pinned
   cudaStream_t setup = nullptr, streams[mb::SERVE_STREAMS] = {};
-  cudaEvent_t setup_ev = nullptr;
   std::vector<cudaEvent_t> slot_ev;  // per view slot: the admitted request's set-up work is done
   bool setup_pending = false;        // a live request's set-up was still running at the last round
   cudaMemPool_t pool = nullptr;  // the server's own pool: freed request memory stays reserved for the next ones
@@ -195,7 +194,6 @@ static size_t req_bytes(const mb_server* S, const mb_request& r) {
 // round takes a request's tiles only once that event has completed, so no
 // round waits for another request's set-up (its probe, with the learned order).
 static int admit_locked(mb_server* S, bool* capped) {
-  bool any = false;
   // A learned admission enqueues a dozen launches; a burst of arrivals is taken a few at a
   // time so that the worker keeps launching rounds in between (*capped: more are waiting).
   int cap = S->learned ? 8 : 1 << 30;
@@ -254,9 +252,7 @@ static int admit_locked(mb_server* S, bool* capped) {
     R.admit_ns = now_ns();
     S->live.push_back(R.id);
     S->ctr.admitted++;
-    any = true;
   }
-  if (any && cudaEventRecord(S->setup_ev, S->setup) != cudaSuccess) return MB_ECUDA;
   return MB_OK;
 }
 
@@ -457,7 +453,6 @@ extern "C" int mb_serve_create(size_t mem_budget_bytes, uint32_t queue_limit, co
             cudaMalloc((void**)&S->d_views, SERVE_SLOTS * sizeof(ViewDesc)) == cudaSuccess &&
             cudaMallocHost((void**)&S->h_view_stage, SERVE_SLOTS * sizeof(ViewDesc)) == cudaSuccess &&
             cudaStreamCreateWithFlags(&S->setup, cudaStreamNonBlocking) == cudaSuccess &&
-            cudaEventCreateWithFlags(&S->setup_ev, cudaEventDisableTiming) == cudaSuccess &&
             cudaMalloc((void**)&S->d_probe_counter, 128 * SERVE_SETUP) == cudaSuccess;
   for (int j = 0; j < SERVE_SETUP && ok && o.learned_order; ++j)
     ok = cudaStreamCreateWithFlags(&S->lsetup[j], cudaStreamNonBlocking) == cudaSuccess;
@@ -469,7 +464,6 @@ extern "C" int mb_serve_create(size_t mem_budget_bytes, uint32_t queue_limit, co
          cudaMalloc((void**)&Rd.d_items, (size_t)S->round_tiles * sizeof(BatchItem)) == cudaSuccess &&
          cudaMalloc((void**)&Rd.d_counter, 256) == cudaSuccess;
   }
-  if (ok) ok = cudaEventRecord(S->setup_ev, S->setup) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     mb_serve_destroy(S);
@@ -647,7 +641,6 @@ extern "C" int mb_serve_destroy(mb_server* S) {
     if (Rd.d_counter) cudaFree(Rd.d_counter);
     if (S->streams[k]) cudaStreamDestroy(S->streams[k]);
   }
-  if (S->setup_ev) cudaEventDestroy(S->setup_ev);
   for (cudaEvent_t e : S->slot_ev)
     if (e) cudaEventDestroy(e);
   if (S->setup) cudaStreamDestroy(S->setup);
