@@ -57,3 +57,26 @@ def test_spearman():
     assert abs(bench.spearman(a, a * 10) - 1.0) < 1e-12
     assert abs(bench.spearman(a, -a) + 1.0) < 1e-12
     assert abs(bench.spearman(a, np.array([2.0, 1.0, 4.0, 3.0])) - 0.6) < 1e-12
+
+
+def test_view_overrides_and_workload_label(monkeypatch):
+    import sys
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse()
+    v = bench.bench_view(a)
+    assert (v.m, v.n, v.iter_max, v.window) == (8192, 8192, 10000, (-2.0, 1.0, -1.5, 1.5))
+    assert bench.bench_config(a, v, 1)["workload"].startswith("8192x8192 re[-2,1] im[-1.5,1.5] iterMax 10000")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--window=-0.2,-0.1,0.05,0.15", "--size", "4096",
+                                      "--iter-max", "2000", "--sched", "fcfs_tiles", "--tile", "16"])
+    a = bench.parse()
+    v = bench.bench_view(a)
+    assert (v.m, v.n, v.iter_max, v.window) == (4096, 4096, 2000, (-0.2, -0.1, 0.05, 0.15))
+    assert "re[-0.2,-0.1] im[0.05,0.15] iterMax 2000" in bench.bench_config(a, v, 1)["workload"]
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--window=1,0,0,1"])
+    a = bench.parse()
+    try:
+        bench.bench_view(a)
+    except SystemExit:
+        pass
+    else:
+        raise AssertionError("an empty window must be refused")
