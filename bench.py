@@ -54,7 +54,11 @@ FP64_PIPE_OPS_PER_ITER = 2.5
 # only while the kernel sources still hash to src_sha1 and the run uses the
 # captured unroll, else null.
 NCU_RENDER = {"src_sha1": "bc9673f8bce11ced2c8ad63c4f07ac1a3053585d", "unroll": 4, "dram_bytes_per_pixel": 3.876,
-              "pipes": {"fp64": 0.802, "alu": 0.795, "fma": 0.280, "issue": 0.732}}
+              "pipes": {"fp64": 0.802, "alu": 0.795, "fma": 0.280, "issue": 0.732},
+              # sm__inst_executed_pipe_fp64.sum x 32 / escape steps of the same launch: the FP64
+              # instructions actually issued per step, idle lanes and replays included (taken at
+              # iterMax 1000, where lanes refill more often than at the benchmark's 10000)
+              "fp64_issued_per_step": 2.56}
 KERNEL_SOURCES = ("escape_core.cuh", "escape_lowp.cuh", "render_kernels.cuh")
 
 
@@ -379,14 +383,16 @@ def measured_hbm_gbs():
         return None
 
 
-def roofline_entry(steps, kernel_ms, peak, traffic):
+def roofline_entry(steps, kernel_ms, peak, traffic, issued_per_step=None):
     """Roofline of the main render launch: `steps` escape steps in `kernel_ms`,
     against the FP64-pipe issue rate `peak` (binary64 ops/s) measured in this run.
     The FP64 pipe carries 2.5 of a step's 8 nominal binary64 ops on average (the
     three additions, less the subtraction of every other step, which runs exactly
     on the integer pipes), so the attainable rate of the 8 ops is peak x 8/2.5,
     as long as the integer pipes keep up (they are co-saturated: ncu shows FP64
-    ~80 % and integer ALU ~80 % busy)."""
+    ~80 % and integer ALU ~80 % busy).  With `issued_per_step` (FP64 instructions that
+    ncu counted per step, idle lanes and replays included) the entry also gives the
+    FP64 pipe's fraction by issued instructions."""
     step_peak = peak * ALG_OPS_PER_ITER / FP64_PIPE_OPS_PER_ITER
     achieved = steps * ALG_OPS_PER_ITER / (kernel_ms * 1e-3)
     return {"bound": "alu", "achieved": achieved / 1e12, "peak": step_peak / 1e12, "unit": "TFLOP/s",
@@ -398,6 +404,8 @@ def roofline_entry(steps, kernel_ms, peak, traffic):
                             "pipes); the products and the doubling run exactly on the integer pipes, "
                             "which are co-saturated with the FP64 pipe" % (peak / 1e12)),
             "fp64_pipe_frac": FP64_PIPE_OPS_PER_ITER * steps / (kernel_ms * 1e-3) / peak,
+            "fp64_pipe_frac_issued": (issued_per_step * steps / (kernel_ms * 1e-3) / peak
+                                      if issued_per_step else None),
             "nominal_frac": achieved / peak,
             "nominal_note": "8 nominal ops per step over the plain FP64-pipe peak (the metric's "
                             "'% of FP64 peak' form, above 1 because 5.5 of the 8 ops are not FP64-pipe "
@@ -665,16 +673,18 @@ def run_ours(args):
     render_iters = iters - probe_iters
     traffic = None
     pipes = None
+    issued = None
     if NCU_RENDER["src_sha1"] == kernel_sha1() and NCU_RENDER["unroll"] == args.unroll:
         traffic = NCU_RENDER["dram_bytes_per_pixel"] * v.m * v.n
         pipes = NCU_RENDER["pipes"]
+        issued = NCU_RENDER["fp64_issued_per_step"]
     line = {
         "metric": "Giter/s", "value": value, "unit": "Giter/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": bench_config(args, v, ws),
         "iterations_per_step": iters,
-        "roofline": dict(roofline_entry(render_iters, kernel_ms, peak, traffic),
+        "roofline": dict(roofline_entry(render_iters, kernel_ms, peak, traffic, issued),
                          ncu_pipe_busy=pipes,
                          ncu_pipe_note="busy fraction of each pipe in the ncu capture of this kernel (8192^2, "
                                        "iterMax 1000): the FP64 pipe's own ceiling is ~0.84 (the peak "

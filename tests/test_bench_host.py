@@ -37,6 +37,10 @@ def test_roofline_entry_arithmetic():
     # on average -> 2.5 x 1.2e11 / 0.6 = 0.5e12 -> the pipe is full
     r = bench.roofline_entry(120_000_000_000, 600.0, 0.5e12, None)
     assert abs(r["fp64_pipe_frac"] - 1.0) < 1e-12
+    assert r["fp64_pipe_frac_issued"] is None
+    # 2.56 FP64 instructions issued per step (idle lanes, replays) on the same launch
+    r2 = bench.roofline_entry(120_000_000_000, 600.0, 0.5e12, None, 2.56)
+    assert abs(r2["fp64_pipe_frac_issued"] - 2.56 / 2.5) < 1e-12
     assert abs(r["frac"] - r["fp64_pipe_frac"]) < 1e-12
     assert abs(r["peak"] - 0.5 * 8 / 2.5) < 1e-12
     assert abs(r["achieved"] - 8 * 1.2e11 / 0.6 / 1e12) < 1e-12
