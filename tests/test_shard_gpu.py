@@ -1,7 +1,8 @@
 """The sharded render's device path on one GPU: the single-rank render through
-the item scheduler against the oracle, and the master gather's pack / unpack
+the item scheduler against the oracle, the master gather's pack / unpack
 kernels (mb_pack_items, mb_unpack_items) against the layout include/mb.h
-states, written out in numpy."""
+states, written out in numpy, and the whole first-come-first-served path with
+two processes (gloo) sharing this GPU."""
 import numpy as np
 import pytest
 
@@ -84,3 +85,67 @@ def test_pack_rejects_items_outside_the_image():
     assert p[0] == 0 and p[tile * tile - 1] == 15 * n + 15
     with pytest.raises(mb.MBError):
         mb.mb_pack_items(img, m, n, 12, items, packed)       # tile not a power of two
+
+
+def _free_port():
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _gpu_rank(rank, world, port, view, q):
+    import os
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    import torch
+    import torch.distributed as dist
+    import paper_2007_00745_gb300 as mb
+    from paper_2007_00745_gb300 import shard
+    torch.cuda.set_device(0)
+    store = shard.make_store(rank, world, timeout_s=120)
+    dist.init_process_group("gloo", store=store, rank=rank, world_size=world)
+    w, m, n, it = view
+    stats = {}
+    img = shard.render_sharded(w, m, n, it, 4.0, tile=32, chunk=6, store=store, stats=stats)
+    torch.cuda.synchronize()
+    same = None
+    if rank == 0:
+        ref = torch.empty(m * n, dtype=torch.int32, device="cuda")
+        mb.mb_render(w, m, n, it, 4.0, ref, sched="fcfs_tiles", tile=16)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(img, ref))
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, same, len(stats["chunks"]), stats["items"]))
+
+
+def test_two_processes_render_one_image_first_come_first_served():
+    """The whole sharded path with the library's kernels: two processes (gloo,
+    both on this GPU -- their render kernels never wait on one another; the
+    store counter on the host is the only coordination) take chunks of 6
+    tiles first come first served, render them with the item scheduler, pack
+    their pixels and send them to rank 0, whose assembled image equals a plain
+    render bit for bit."""
+    import torch.multiprocessing as mp
+    view = ((-2.0, 1.0, -1.5, 1.5), 700, 900, 3000)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_gpu_rank, args=(r, 2, port, view, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        res = sorted(q.get(timeout=300) for _ in range(2))
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.kill()
+    assert all(p.exitcode == 0 for p in procs)
+    n_tiles = (-(-700 // 32)) * (-(-900 // 32))
+    assert res[0][1] is True
+    assert res[0][3] + res[1][3] == n_tiles          # every tile rendered once
+    assert res[0][2] >= 1 and res[1][2] >= 1         # both ranks took chunks
